@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Converged plans/s of batched ADMM planning on one B300 (and N replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg1|cfg2|cfg0]
+    python bench.py --impl reference ...     # the FP64 CPU oracle on host cores
+
+A step is one solve of the whole hot path over one batch of weightings: K
+weightings of the 9x9 (cfg1) or 21x21 (cfg2) slider grid, iterated on the
+device until every column meets the residual tolerance (1e-4), with the case
+(A, S^{-1}) resident.  `value` = converged plans / device time of the timed
+steps.  `e2e` times the whole C-ABI round trip per step from pinned host
+buffers: create_case (phi host->device, assembly, scaling, S, Cholesky,
+inverse), the solve, and fetch_times (device->host).
+
+The workload is synthetic (seeded generator `synth.cases`): the paper's patient
+cases are not public.  Multi-GPU runs are independent replicas (one case per
+rank, no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {"cfg0": 0, "cfg1": 1, "cfg2": 2, "cfg3": 3}
+METRIC = "converged plans/s (81 & 441 weightings) vs plain FP32 form; p50/p99 latency"
+PAPER_ITERS = 3000          # fixed iterations per pass in the paper (Sec. 3.D)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p["bf16_tflops"], p["bf16_tflops_sustained"], "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+def kernel_work(name, m, n, K):
+    """Algorithmic (bytes, flops) of one launch of an iteration kernel."""
+    if name == "gemm1":      # A . R1: A as 2 bf16 terms once, R1 hi/lo, rhs out
+        return 4 * m * n + 4 * n * K + 4 * m * K, 2 * m * n * K
+    if name == "solve":      # S^{-1} . rhs: S^{-1} as 3 bf16 parts, rhs 3 parts, v out
+        return 6 * m * m + 6 * m * K + 4 * m * K, 2 * m * m * K
+    if name == "gemm2":      # A^T . V + q1 update: A (2 terms) once, V hi/lo, q1 r/w, R1 out
+        return 4 * m * n + 4 * m * K + 12 * n * K, 2 * m * n * K
+    if name in ("reduce_rhs", "reduce_solve"):
+        return 16 * m * K, 0
+    return 0, 0
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, idx):
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_inputs(cfg):
+    from synth import cases as SC
+    case = SC.workload_case(cfg)
+    W = SC.slider_weights(SC.WORKLOADS[cfg]["grid"])
+    return case, W
+
+
+def oracle_sample(case, W, iters_to_converge, budget_s=30.0):
+    """Time the FP64 oracle ADMM (as it stands) on the host cores: a bounded
+    number of iterations over all K columns; per-iteration time is the
+    difference to a zero-iteration run (which still forms and factors S)."""
+    from oracle import admm as AD
+    from oracle import lp as L
+    from synth import cases as SC
+    lp = L.precondition(L.assemble_case(case))
+    b, l, u = L.bounds(lp, W)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    t0 = time.perf_counter()
+    AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=0)
+    t_setup = time.perf_counter() - t0
+    n_it = 2
+    t0 = time.perf_counter()
+    AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=n_it)
+    t_run = time.perf_counter() - t0
+    t_iter = max((t_run - t_setup) / n_it, 1e-9)
+    K = W.shape[0]
+    cores = len(os.sched_getaffinity(0))
+    return dict(value=K / (t_iter * iters_to_converge), unit="plans/s", cores=cores,
+                kind="oracle",
+                sample=(f"FP64 oracle ADMM (numpy/LAPACK) on {case.name}, all {K} weightings, "
+                        f"{n_it} iterations timed after S formation+Cholesky ({t_setup:.1f} s, "
+                        f"excluded like the device's case set-up); {t_iter * 1e3:.1f} ms/iteration "
+                        f"extrapolated to {iters_to_converge:.0f} iterations per plan"))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cfg = WORKLOADS[args.workload]
+    case, W = make_inputs(cfg)
+    K = W.shape[0]
+    from oracle import admm as AD
+    from oracle import lp as L
+    from synth import cases as SC
+    lp = L.precondition(L.assemble_case(case))
+    b, l, u = L.bounds(lp, W)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    t0 = time.perf_counter()
+    AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=0)
+    t_setup = time.perf_counter() - t0
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=1)
+        dt = time.perf_counter() - t0 - t_setup
+        if s >= args.warmup:
+            times.append(max(dt, 1e-9))
+    t_iter = statistics.median(times)
+    value = K / (t_iter * PAPER_ITERS)
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "plans/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_iter * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(case, W, args),
+            "cpu_baseline": {"value": value, "unit": "plans/s", "cores": cores, "kind": "oracle",
+                             "sample": (f"one FP64 oracle ADMM iteration over all {K} weightings "
+                                        f"per step (S formation+Cholesky, {t_setup:.1f} s, "
+                                        f"subtracted), extrapolated to the paper's fixed "
+                                        f"{PAPER_ITERS} iterations (Sec. 3.D)")},
+            "e2e": {"value": value, "unit": "plans/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(case, W, args):
+    m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
+    return {"workload": f"{case.name} (A {m}x{n}, K={W.shape[0]} weightings, tol {args.tol:g})",
+            "m": m, "n": n, "K": int(W.shape[0]), "tol": args.tol,
+            "precision": ("bf16x3: A as 2 bf16 terms, iterates 2 bf16 terms (3 products per GEMM); "
+                          "S^-1 and solve input 3 bf16 terms (6 products); fp32 accumulate"),
+            "rho": "Eq. rho_rule, rho0 = 2500", "l2": "inputs larger than L2 (A resident, "
+            f"{4 * m * n / 1e6:.0f} MB as 2 bf16 terms > 126 MB)", "parallelism": "replicas"}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("tc_gemm.cu", "iter_ctx.cuh", "iter.cu"):
+        with open(os.path.join(ROOT, "paper_2509_08602_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source
+    is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[workload][kernel]
+        return e["bytes_per_launch"] if e.get("source_hash") == kernel_hash() else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2509_08602_b300 import build
+    if rank == 0:
+        build.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    from paper_2509_08602_b300 import lgk
+    cfg = WORKLOADS[args.workload]
+    case, W = make_inputs(cfg)
+    K = W.shape[0]
+    params = lgk.default_params(precision=lgk.PREC_BF16X3, device=local, profile=1)
+    from synth import cases as SC
+    rule = dict(w0_bot=SC.W0_BOT, rho0=2.5e3, tol=args.tol, max_iter=args.max_iter)
+    cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                         case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                         params=params)
+    for _ in range(args.warmup):
+        r = lgk.solve_weightings(cs, W, None, **rule)
+        r.close()
+    lgk.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prof = {k: [0.0, 0] for k in lgk.KERNELS}
+    conv = 0
+    iters = []
+    lat = []
+    ev0.record()
+    t_host0 = time.perf_counter()
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        r = lgk.solve_weightings(cs, W, None, **rule)
+        lat.append(time.perf_counter() - t1)
+        st = lgk.fetch_stats(r)
+        conv += int(st["converged"].sum())
+        iters.append(st["iters"])
+        for k, (ms, nl) in lgk.fetch_profile(r).items():
+            prof[k][0] += ms
+            prof[k][1] += nl
+        r.close()
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = lgk.launch_count()
+    clk = clocks.stop()
+    host_s = time.perf_counter() - t_host0
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    # the library solves on its own stream; the host-blocking solve brackets it
+    step_s = max(dev_s, host_s)
+    t_max = allreduce_max(step_s, world)
+    conv_all = allreduce_sum(conv, world)
+    value = conv_all / t_max
+    mean_iters = float(np.mean(np.concatenate(iters)))
+
+    # e2e: pinned host inputs, create + solve + fetch per step
+    phi_pinned = torch.empty(case.phi.shape, dtype=torch.float64, pin_memory=True).numpy()
+    phi_pinned[...] = case.phi
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv_e2e = 0
+    for _ in range(e2e_steps):
+        c2 = lgk.create_case(phi_pinned, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                             case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                             params=lgk.default_params(precision=lgk.PREC_BF16X3, device=local))
+        r = lgk.solve_weightings(c2, W, None, **rule)
+        t, tau = lgk.fetch_times(r)
+        conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
+        r.close()
+        c2.close()
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    e2e_value = allreduce_sum(conv_e2e, world) / e2e_s
+    h2d = case.phi.nbytes + case.kind.nbytes + case.struct_id.nbytes + W.nbytes
+    d2h = t.nbytes + tau.nbytes
+
+    out = None
+    if rank == 0:
+        # plain FP32 GPU form, same workload and tolerance (comparison form)
+        fp32 = None
+        if not args.no_fp32:
+            c3 = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                                 case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                                 params=lgk.default_params(precision=lgk.PREC_FP32, device=local))
+            r = lgk.solve_weightings(c3, W, None, **rule)
+            r.close()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = lgk.solve_weightings(c3, W, None, **rule)
+            dt = time.perf_counter() - t0
+            s3 = lgk.fetch_stats(r)
+            fp32 = {"value": float(s3["converged"].sum()) / dt, "unit": "plans/s",
+                    "mean_iters": float(s3["iters"].mean()),
+                    "all_converged": bool(s3["converged"].all()),
+                    "ratio_bf16x2_over_fp32": (value / world) / (float(s3["converged"].sum()) / dt)}
+            r.close()
+            c3.close()
+        hbm, tf_burst, tf_sus, src = peaks()
+        m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
+        dom = max(prof, key=lambda k: prof[k][0])
+        ms_avg = prof[dom][0] / max(prof[dom][1], 1)
+        nbytes, flops = kernel_work(dom, m, n, K)
+        intensity = flops / max(nbytes, 1)
+        ridge = tf_sus * 1e12 / (hbm * 1e9)
+        if intensity < ridge:
+            achieved = nbytes / (ms_avg / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s"}
+        else:
+            achieved = flops / (ms_avg / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": tf_sus, "unit": "TFLOP/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = committed_traffic(dom, args.workload)
+        roof["kernel"] = dom
+        roof["peak_source"] = f"{src} (MEASURED_PEAKS.json)" if src == "measured" else "fallback"
+        roof["algorithmic_bytes_per_launch"] = nbytes
+        roof["algorithmic_flops_per_launch"] = flops
+        roof["avg_launch_ms"] = ms_avg
+        total_ms = sum(v[0] for v in prof.values())
+        roof["kernel_share"] = {k: round(v[0] / total_ms, 4) for k, v in prof.items()}
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = oracle_sample(case, W, mean_iters)
+        lat_ms = sorted(x * 1e3 for x in lat)
+        out = {"metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "bf16", "data": "synthetic (seeded generator; paper cases are not public)",
+               "config": workload_config(case, W, args),
+               "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h),
+                       "note": "create_case from pinned host phi + solve + fetch_times"},
+               "gpu_launches": int(launches),
+               "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
+               "latency_ms": {"p50": lat_ms[len(lat_ms) // 2],
+                              "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
+               "mean_iters_per_plan": mean_iters, "converged_fraction": conv / (K * args.steps),
+               "fp32_form": fp32}
+        print(json.dumps(out), flush=True)
+    cs.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1", choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--max-iter", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_init()
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

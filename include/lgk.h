@@ -1,0 +1,207 @@
+/*
+ * lgk.h -- C ABI of the batched-ADMM Gamma Knife planning library (liblgk.so).
+ *
+ * Solves the dual linear program of Lightning inverse planning (arXiv
+ * 2509.08602, Eq. dual_problem and Appendix A)
+ *
+ *     minimize c^T x   subject to   A x <= b,   l <= x <= u
+ *
+ * for K objective weightings at once with the scaled-form ADMM of Sec. 2.B
+ * (Eq. admm, with the x-step in the closed form of Eq. partial_elimination),
+ * all K weightings sharing one matrix A and one cached inverse of
+ * S = A A^T + I.  Everything runs on one CUDA device.
+ *
+ * Conventions (every entry point):
+ *  - The return value is an lgk_status; 0 is success.  No C++ exception and no
+ *    abort crosses this boundary.  On failure lgk_last_error() returns a
+ *    thread-local message describing the last error.
+ *  - Input arrays are HOST pointers owned by the caller; the library copies
+ *    what it needs before returning and never keeps a caller pointer.
+ *  - Output arrays are HOST pointers owned by the caller, sized as stated.
+ *  - lgk_case and lgk_result are opaque and owned by the library until
+ *    lgk_destroy_case / lgk_free_result.  A result keeps its case alive
+ *    (a case may be destroyed while results of it exist).
+ *  - One lgk_case may be used by one host thread at a time.  Different cases
+ *    may be used concurrently from different threads.
+ *  - All arrays are row-major (C order).
+ */
+#ifndef LGK_H
+#define LGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lgk_case lgk_case;
+typedef struct lgk_result lgk_result;
+
+typedef enum {
+    LGK_OK = 0,
+    LGK_EINVAL = 1,    /* invalid argument (sizes, NaN/Inf, class codes, ...)      */
+    LGK_ENOMEM = 2,    /* device or host allocation failed                         */
+    LGK_EBUDGET = 3,   /* case footprint exceeds lgk_params.hbm_budget             */
+    LGK_ENOTPD = 4,    /* S = A A^T + I not positive definite in FP64 (Cholesky)   */
+    LGK_ECUDA = 5,     /* CUDA runtime/driver error, or a device-side error flag   */
+    LGK_ETIMEOUT = 6   /* a bounded wait (host poll or device barrier) ran out     */
+} lgk_status;
+
+/* Dose-point classes (Sec. 2.A; Appendix A block names TS, TI, R, LD, O). */
+enum { LGK_TS = 0, LGK_TI = 1, LGK_R = 2, LGK_LD1 = 3, LGK_LD2 = 4, LGK_OAR = 5 };
+
+/* Arithmetic of the ADMM iterations.
+ *  LGK_PREC_FP32:   A, S^{-1} and the iterates in FP32, all GEMMs in FP32 on
+ *                   CUDA cores through cuBLAS (the plain GPU form, the
+ *                   paper's own precision: Sec. 3.A).  Comparison form.
+ *  LGK_PREC_BF16:   A rounded once to BF16 (8 significant bits), iterates as
+ *                   two BF16 terms, 2 tensor-core products per GEMM.  Fast,
+ *                   but the LP solved is the one with the rounded matrix: on
+ *                   the synthetic cases its plans' beam-on time moves ~1 %.
+ *  LGK_PREC_BF16X3: A as two BF16 terms (hi + lo, ~16 bits) and the iterates
+ *                   as two BF16 terms, 3 products per GEMM (hi.hi + hi.lo +
+ *                   lo.hi); the plans match FP64 ones.  Product form, default.
+ *  In both BF16 forms S^{-1} and the solve input are split into three BF16
+ *  terms (6 products), accumulation is FP32 in tensor memory, and S is formed
+ *  and inverted in FP64 from exactly the matrix the GEMMs use.               */
+enum { LGK_PREC_FP32 = 0, LGK_PREC_BF16 = 1, LGK_PREC_BF16X3 = 2 };
+
+typedef struct {
+    int n_iso;               /* N isocenters; beam variables B = 24 N (8 sectors x 3 collimators) */
+    int n_pts;               /* P dose points                                                   */
+    int n_targets;           /* >= 1; TS/TI/R points carry a target index                       */
+    int n_oars;              /* >= 0; OAR points carry an OAR index                             */
+    const double* phi;       /* P x B dose-rate kernels, Gy/min.  Beam index
+                                b = (i*8 + s)*3 + c (isocenter, sector, collimator)             */
+    const uint8_t* kind;     /* P point classes LGK_TS..LGK_OAR                                 */
+    const uint16_t* struct_id; /* P: target index (TS/TI/R), OAR index (OAR), ignored (LD)      */
+    const double* d_presc;   /* n_targets prescription doses D_T (> 0), Gy                      */
+    const double* q_area;    /* n_targets shares of total target area   (Appendix A, q_kA)      */
+    const double* q_vol;     /* n_targets shares of total target volume (Appendix A, q_kV)      */
+    const double* d_oar;     /* n_oars maximum doses D_O (> 0), Gy; may be NULL if n_oars = 0   */
+    double d_ld1, d_ld2;     /* low-dose thresholds (> 0), Gy (Appendix A)                      */
+    double phi_cal;          /* calibration dose rate, Gy/min (3 in Sec. 3.B)                   */
+} lgk_case_desc;
+
+typedef struct {
+    int precision;           /* LGK_PREC_*; default LGK_PREC_BF16X3                             */
+    int normalize_rows;      /* Sec. 3.C unit-norm rows of A (scales b too); default 1          */
+    int scale_bot;           /* Sec. 3.C beta scaling of the BOT columns; default 1             */
+    int check_every;         /* iterations between residual tests; default 10                   */
+    double eps_abs;          /* absolute residual floor per sqrt(n+m); default 1e-12            */
+    int device;              /* CUDA device ordinal; default 0                                   */
+    void* stream;            /* cudaStream_t to run on, or NULL for a library-owned stream     */
+    size_t hbm_budget;       /* bytes; 0 = no limit.  create_case fails with LGK_EBUDGET when
+                                the case's resident footprint would exceed it                  */
+    int timeout_ms;          /* bound on any single host wait; default 600000                   */
+    int profile;             /* 1: time every kernel of every iteration with CUDA events
+                                (read by lgk_fetch_profile); default 0                       */
+} lgk_params;
+
+/* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
+int lgk_default_params(lgk_params* p);
+
+/*
+ * lgk_create_case -- assemble and prepare one planning case on the device.
+ *
+ * Builds A of Appendix A (rows: 24 N beam variables then N isocenter rows;
+ * columns: the P points in input order then 8 N BOT columns):
+ *   A = [ phi_TS^T/D  phi_TI^T/D  -phi_R^T/D  -phi_LD^T/D_LD  -phi_O^T/D_O  -C_S^T ]
+ *       [     0           0           0            0              0         T^T   ]
+ * with C = I_N (x) I_8 (x) 1_{1x3}, T = I_N (x) 1_{8x1}, C_S = C phi_cal / D_T,mean;
+ * normalises its rows and scales the BOT columns by
+ * beta = (#non-OAR points)/2000 (Sec. 3.C); forms S = A A^T + I in FP64,
+ * factors it (FP64 Cholesky, Sec. 2.B "cache a decomposition") and keeps its
+ * inverse resident (Sec. 3.A keeps the explicit inverse).
+ *
+ * desc, p: host structs (p may be NULL for defaults).  *out receives the case.
+ * Errors: LGK_EINVAL (bad sizes/classes/NaN), LGK_EBUDGET, LGK_ENOMEM,
+ * LGK_ENOTPD, LGK_ECUDA.  On error *out is set to NULL.
+ */
+int lgk_create_case(const lgk_case_desc* desc, const lgk_params* p, lgk_case** out);
+
+/* Sizes of a case: m rows, n columns of A, beta applied, device bytes held. */
+int lgk_case_info(const lgk_case* cs, int* m, int* n, double* beta, size_t* bytes);
+
+/*
+ * lgk_solve_weightings -- run batched ADMM for K weightings (Sec. 2.B).
+ *
+ * W:   K x 4 host array (w_T, w_R, w_LD, w_BOT) >= 0 per weighting (Sec. 2.A).
+ *      Bounds per Appendix A: u = (q_kA w_T / N_kTS, q_kV w_T / N_kTI,
+ *      (w_R / n_targets) / N_kR, w_LD / N_LD1, w_LD / N_LD2, inf, inf),
+ *      l = 0, b = (0, w_BOT) (times the row scale).
+ * rho: K host values > 0, or NULL for the rule of Eq. rho_rule,
+ *      rho = rho0 * sqrt(w0_bot / w_BOT) (w0_bot, rho0 > 0 then required).
+ * tol: relative primal/dual residual tolerance of the stop test; 0 runs
+ *      exactly max_iter iterations for every column.
+ * max_iter: > 0.  State starts at zero (z = y = 0).
+ * Stop test (every check_every iterations, per column): with r = x - z and
+ *   s = rho (z - z_prev), stop once ||r|| <= eps_abs sqrt(n+m) + tol max(||x||,||z||)
+ *   and ||s|| <= eps_abs sqrt(n+m) + tol ||rho y||.  A stopped column is frozen.
+ * Blocks until every column has stopped or reached max_iter.
+ * *out receives the result (library-owned).  Non-convergence is reported per
+ * column by lgk_fetch_stats, not as an error.
+ * Errors: LGK_EINVAL, LGK_ENOMEM, LGK_ECUDA, LGK_ETIMEOUT.
+ */
+int lgk_solve_weightings(lgk_case* cs, int K, const double* W, const double* rho,
+                         double w0_bot, double rho0, double tol, int max_iter,
+                         lgk_result** out);
+
+/* Sector times t (K x 24N, minutes) and isocenter beam-on times tau (K x N,
+ * normalised units of the LP) of each plan: the multipliers rho * y2 of
+ * A x <= b, unscaled by the row scale (Sec. 2.B: the primal solution is rho y*).
+ * Either pointer may be NULL. */
+int lgk_fetch_times(const lgk_result* res, double* t, double* tau);
+
+/* Doses of each plan on caller points: dose = phi_eval t (Sec. 4: the dose is
+ * the dose-rate kernels weighted by the sector times).  phi_eval is n_eval x 24N
+ * (host), dose is K x n_eval (host).  Computed on the device in FP64. */
+int lgk_fetch_doses(const lgk_result* res, const double* phi_eval, int n_eval, double* dose);
+
+/* Per-column statistics (each pointer may be NULL; arrays of K):
+ * iterations run, dual objective c^T z1 (FP64 on the device), relative primal
+ * and dual residuals at the last test, converged flag. */
+int lgk_fetch_stats(const lgk_result* res, int* iters, double* obj, double* rel_pri,
+                    double* rel_dual, uint8_t* converged);
+
+/*
+ * lgk_solve_weightings_warm -- as lgk_solve_weightings, but starting from a
+ * given ADMM state instead of zero (checkpoint / resume, or a warm start from
+ * an earlier solve).  The state is the q-form of Eq. admm: q1 = z1 + y1
+ * (K x n) and q2 = z2 + y2 (K x m) of the scaled problem, FP64 host arrays as
+ * returned by lgk_fetch_state; z = projection of q (z1 = clip(q1, 0, u),
+ * z2 = min(q2, b)) and y = q - z.  Either pointer may be NULL (zeros).
+ */
+int lgk_solve_weightings_warm(lgk_case* cs, int K, const double* W, const double* rho,
+                              double w0_bot, double rho0, double tol, int max_iter,
+                              const double* q1_init, const double* q2_init, lgk_result** out);
+
+/* ADMM state of the scaled problem in q-form: q1 = z1 + y1 (K x n) and
+ * q2 = z2 + y2 (K x m), FP64 host arrays (either may be NULL).  Feeding them
+ * back to lgk_solve_weightings_warm resumes the iteration. */
+int lgk_fetch_state(const lgk_result* res, double* q1, double* q2);
+
+/* Kernel classes of one ADMM iteration, in launch order. */
+enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLVE = 3,
+       LGK_K_GEMM2 = 4, LGK_K_FINALIZE = 5, LGK_K_COUNT = 6 };
+
+/* Per-kernel-class device time of a solve made with lgk_params.profile = 1:
+ * ms[LGK_K_COUNT] total milliseconds between CUDA events recorded on the
+ * solve's stream around each kernel, launches[LGK_K_COUNT] the number of
+ * timed launches (iterations in which columns were still active).  Either
+ * pointer may be NULL.  LGK_EINVAL if the solve was not profiled. */
+int lgk_fetch_profile(const lgk_result* res, double* ms, long long* launches);
+
+void lgk_free_result(lgk_result* res);
+void lgk_destroy_case(lgk_case* cs);
+const char* lgk_last_error(void);
+
+/* Number of kernel launches the library issued on this thread since the last
+ * call (diagnostics for launch counting; graph replays count their nodes). */
+long long lgk_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LGK_H */

@@ -1,0 +1,263 @@
+// C ABI of liblgk: argument checking, handle ownership, error reporting.
+#include <math.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "lgk_impl.hpp"
+
+struct lgk_case {
+    std::shared_ptr<lgk::CaseData> d;
+};
+struct lgk_result {
+    std::unique_ptr<lgk::ResultData> d;
+};
+
+namespace lgk {
+
+static thread_local std::string g_err;
+static thread_local long long g_launches = 0;
+
+void set_error(const std::string& msg) { g_err = msg; }
+void count_launch(long long n) { g_launches += n; }
+
+CaseData::~CaseData() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (cublas) cublasDestroy(cublas);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+static int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+static bool finite_nonneg(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(a[i] >= 0.0) || !isfinite(a[i])) return false;
+    return true;
+}
+
+static bool finite_pos(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!(a[i] > 0.0) || !isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace lgk
+
+using namespace lgk;
+
+extern "C" {
+
+int lgk_default_params(lgk_params* p) {
+    if (!p) return fail(LGK_EINVAL, "lgk_default_params: p is NULL");
+    p->precision = LGK_PREC_BF16X3;
+    p->normalize_rows = 1;
+    p->scale_bot = 1;
+    p->check_every = 10;
+    p->eps_abs = 1e-12;
+    p->device = 0;
+    p->stream = nullptr;
+    p->hbm_budget = 0;
+    p->timeout_ms = 600000;
+    p->profile = 0;
+    return LGK_OK;
+}
+
+int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out) {
+    if (!out) return fail(LGK_EINVAL, "lgk_create_case: out is NULL");
+    *out = nullptr;
+    if (!d) return fail(LGK_EINVAL, "lgk_create_case: desc is NULL");
+    lgk_params prm;
+    lgk_default_params(&prm);
+    if (p) prm = *p;
+    if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
+        prm.precision != LGK_PREC_BF16X3)
+        return fail(LGK_EINVAL, "unknown precision");
+    if (prm.check_every < 1 || !(prm.eps_abs >= 0.0) || prm.timeout_ms < 1)
+        return fail(LGK_EINVAL, "check_every >= 1, eps_abs >= 0 and timeout_ms >= 1 required");
+    if (d->n_iso < 1 || d->n_pts < 1 || d->n_targets < 1 || d->n_targets > kMaxTargets || d->n_oars < 0)
+        return fail(LGK_EINVAL, "need n_iso >= 1, n_pts >= 1, 1 <= n_targets <= 64, n_oars >= 0");
+    const long long B = 24LL * d->n_iso, m = B + d->n_iso, n = (long long)d->n_pts + 8LL * d->n_iso;
+    if (round_up(m, 128) * round_up(n, 128) >= (1LL << 40) || n >= (1LL << 30))
+        return fail(LGK_EINVAL, "problem too large");
+    if (!d->phi || !d->kind || !d->struct_id || !d->d_presc || !d->q_area || !d->q_vol ||
+        (d->n_oars > 0 && !d->d_oar))
+        return fail(LGK_EINVAL, "NULL input array");
+    if (!finite_pos(d->d_presc, d->n_targets) || !finite_nonneg(d->q_area, d->n_targets) ||
+        !finite_nonneg(d->q_vol, d->n_targets) || (d->n_oars && !finite_pos(d->d_oar, d->n_oars)) ||
+        !(d->d_ld1 > 0) || !(d->d_ld2 > 0) || !(d->phi_cal > 0) || !isfinite(d->d_ld1) ||
+        !isfinite(d->d_ld2) || !isfinite(d->phi_cal))
+        return fail(LGK_EINVAL, "thresholds must be finite and > 0, q shares finite and >= 0");
+    for (int i = 0; i < d->n_pts; ++i) {
+        int k = d->kind[i], s = d->struct_id[i];
+        if (k > LGK_OAR) return fail(LGK_EINVAL, "point " + std::to_string(i) + ": unknown class");
+        if (k <= LGK_R && s >= d->n_targets)
+            return fail(LGK_EINVAL, "point " + std::to_string(i) + ": target index out of range");
+        if (k == LGK_OAR && s >= d->n_oars)
+            return fail(LGK_EINVAL, "point " + std::to_string(i) + ": OAR index out of range");
+    }
+    if (!finite_nonneg(d->phi, (size_t)d->n_pts * B))
+        return fail(LGK_EINVAL, "phi must be finite and >= 0");
+
+    std::shared_ptr<CaseData> cs;
+    try {
+        cs = std::make_shared<CaseData>();
+    } catch (const std::bad_alloc&) {
+        return fail(LGK_ENOMEM, "host allocation failed");
+    }
+    cs->prm = prm;
+    cs->device = prm.device;
+    LGK_CUDA_TRY(cudaSetDevice(prm.device));
+    if (prm.stream) {
+        cs->stream = static_cast<cudaStream_t>(prm.stream);
+    } else {
+        LGK_CUDA_TRY(cudaStreamCreateWithFlags(&cs->stream, cudaStreamNonBlocking));
+        cs->own_stream = true;
+    }
+    if (prm.precision == LGK_PREC_FP32) {
+        if (cublasCreate(&cs->cublas) != CUBLAS_STATUS_SUCCESS) return fail(LGK_ECUDA, "cublasCreate failed");
+        cublasSetMathMode(cs->cublas, CUBLAS_PEDANTIC_MATH);     // strict FP32, no TF32
+        cublasSetStream(cs->cublas, cs->stream);
+        int rc = cs->cublas_ws.alloc(32u << 20);
+        if (rc) return rc;
+        cublasSetWorkspace(cs->cublas, cs->cublas_ws.p, cs->cublas_ws.bytes);
+    }
+    int rc;
+    try {
+        rc = setup_case(*cs, *d);
+    } catch (const std::bad_alloc&) {
+        rc = fail(LGK_ENOMEM, "host allocation failed");
+    }
+    if (rc) return rc;
+    lgk_case* h = new (std::nothrow) lgk_case;
+    if (!h) return fail(LGK_ENOMEM, "host allocation failed");
+    h->d = std::move(cs);
+    *out = h;
+    return LGK_OK;
+}
+
+int lgk_case_info(const lgk_case* c, int* m, int* n, double* beta, size_t* bytes) {
+    if (!c) return fail(LGK_EINVAL, "case is NULL");
+    if (m) *m = c->d->m;
+    if (n) *n = c->d->n;
+    if (beta) *beta = c->d->beta;
+    if (bytes) *bytes = c->d->bytes_held();
+    return LGK_OK;
+}
+
+int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
+                              double rho0, double tol, int max_iter, const double* q1_init,
+                              const double* q2_init, lgk_result** out) {
+    if (!out) return fail(LGK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
+    if (K < 1 || K > 4096) return fail(LGK_EINVAL, "need 1 <= K <= 4096");
+    if (!finite_nonneg(W, (size_t)K * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
+    if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
+    std::vector<double> r(K);
+    if (rho) {
+        if (!finite_pos(rho, K)) return fail(LGK_EINVAL, "rho must be finite and > 0");
+        r.assign(rho, rho + K);
+    } else {
+        if (!(w0_bot > 0) || !(rho0 > 0) || !isfinite(w0_bot) || !isfinite(rho0))
+            return fail(LGK_EINVAL, "rho rule needs w0_bot > 0 and rho0 > 0");
+        for (int j = 0; j < K; ++j) {
+            if (!(W[4 * j + 3] > 0)) return fail(LGK_EINVAL, "rho rule needs w_BOT > 0");
+            r[j] = rho0 * sqrt(w0_bot / W[4 * j + 3]);     // Eq. rho_rule
+        }
+    }
+    LGK_CUDA_TRY(cudaSetDevice(c->d->device));
+    std::unique_ptr<ResultData> res;
+    try {
+        res.reset(new ResultData);
+    } catch (const std::bad_alloc&) {
+        return fail(LGK_ENOMEM, "host allocation failed");
+    }
+    res->cs = c->d;
+    res->K = K;
+    res->tol = tol;
+    res->max_iter = max_iter;
+    if ((q1_init && !std::all_of(q1_init, q1_init + (size_t)K * c->d->n, [](double v) { return isfinite(v); })) ||
+        (q2_init && !std::all_of(q2_init, q2_init + (size_t)K * c->d->m, [](double v) { return isfinite(v); })))
+        return fail(LGK_EINVAL, "initial state must be finite");
+    int rc;
+    try {
+        rc = run_solve(*res, W, r.data(), q1_init, q2_init);
+    } catch (const std::bad_alloc&) {
+        rc = fail(LGK_ENOMEM, "host allocation failed");
+    }
+    if (rc) return rc;
+    lgk_result* h = new (std::nothrow) lgk_result;
+    if (!h) return fail(LGK_ENOMEM, "host allocation failed");
+    h->d = std::move(res);
+    *out = h;
+    return LGK_OK;
+}
+
+int lgk_solve_weightings(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
+                         double rho0, double tol, int max_iter, lgk_result** out) {
+    return lgk_solve_weightings_warm(c, K, W, rho, w0_bot, rho0, tol, max_iter, nullptr, nullptr, out);
+}
+
+int lgk_fetch_times(const lgk_result* r, double* t, double* tau) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
+    return fetch_times(*r->d, t, tau);
+}
+
+int lgk_fetch_doses(const lgk_result* r, const double* phi_eval, int n_eval, double* dose) {
+    if (!r || !phi_eval || !dose || n_eval < 1) return fail(LGK_EINVAL, "bad fetch_doses arguments");
+    if (!finite_nonneg(phi_eval, (size_t)n_eval * r->d->cs->n_beams))
+        return fail(LGK_EINVAL, "phi_eval must be finite and >= 0");
+    LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
+    return fetch_doses(*r->d, phi_eval, n_eval, dose);
+}
+
+int lgk_fetch_stats(const lgk_result* r, int* iters, double* obj, double* rel_pri, double* rel_dual,
+                    uint8_t* converged) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
+    return fetch_stats(*r->d, iters, obj, rel_pri, rel_dual, converged);
+}
+
+int lgk_fetch_state(const lgk_result* r, double* q1, double* q2) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
+    return fetch_state(*r->d, q1, q2);
+}
+
+int lgk_fetch_profile(const lgk_result* r, double* ms, long long* launches) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (!r->d->cs->prm.profile) return fail(LGK_EINVAL, "solve was not profiled (lgk_params.profile = 0)");
+    for (int k = 0; k < LGK_K_COUNT; ++k) {
+        if (ms) ms[k] = r->d->prof_ms[k];
+        if (launches) launches[k] = r->d->prof_n[k];
+    }
+    return LGK_OK;
+}
+
+void lgk_free_result(lgk_result* r) {
+    if (!r) return;
+    cudaSetDevice(r->d->cs->device);
+    delete r;
+}
+
+void lgk_destroy_case(lgk_case* c) {
+    if (!c) return;
+    cudaSetDevice(c->d->device);
+    delete c;
+}
+
+const char* lgk_last_error(void) { return g_err.c_str(); }
+
+long long lgk_launch_count(void) {
+    long long n = g_launches;
+    g_launches = 0;
+    return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,643 @@
+// One ADMM solve over K weightings (Sec. 2.B), in the q-form used on the
+// device.  With q1 = x1 + y1_prev and q2 = x2 + y2_prev, z = P(q) and
+// y = q - P(q), and one iteration of Eq. admm (x-step in the closed form of
+// Eq. partial_elimination) reads
+//     rhs = A (2 P1(q1) - q1 - c/rho) + q2 - 2 P2(q2)
+//     v   = S^{-1} rhs
+//     q1' = P1(q1) - c/rho - A^T v,      q2' = v + P2(q2)
+// with P1 = clip to [0, u] and P2 = min(., b).  The state is one n x K and one
+// m x K matrix; weightings are the K columns.
+//
+// Kernel sequence of one iteration (both precisions):
+//   GEMM1  part  = A . R1            (split over the n columns of A)
+//   reduce rhs   = sum(part) + q2 - 2 P2(q2)
+//   solve  part  = S^{-1} . rhs      (split over m)
+//   reduce q2'   = sum(part) + P2(q2), residual partials of the m-block
+//   GEMM2  q1'   = P1(q1) - c/rho - A^T v, R1' for the next GEMM1, residual
+//                  partials of the n-block
+//   finalize     per-column stop test (Boyd et al. Sec. 3.3), freeze
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <thread>
+#include <vector>
+
+#include "lgk_impl.hpp"
+#include "iter_ctx.cuh"
+
+namespace lgk {
+
+ResultData::~ResultData() {
+    if (cs && cs->stream) cudaStreamSynchronize(cs->stream);
+    if (graph) cudaGraphExecDestroy(graph);
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+}
+
+// Event between kernels k-1 and k of captured iteration `it` (profile mode).
+static void prof_mark(ResultData& r, int it, int k) {
+    // External: captured as an event-record node of the graph (a plain record
+    // inside a capture only expresses a dependency)
+    if (!r.prof_ev.empty())
+        cudaEventRecordWithFlags(r.prof_ev[(size_t)it * 7 + k], r.cs->stream, cudaEventRecordExternal);
+}
+
+// ---------------------------------------------------------------- helpers
+
+// block-wide sum of 5 values into out[0..4] (thread 0 holds the result)
+__device__ inline void block_sum5(float v[5], double* out) {
+    __shared__ float red[5][32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[k][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < nw; ++i) s += (double)red[k][i];
+            out[k] = s;
+        }
+    }
+}
+
+// R1 = 2 P1(q1) - q1 - c/rho for the first GEMM1 (q1 = 0 at the start).
+template <bool BF16>
+__global__ void k_init_r1(IterCtx cx, void* R1) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (p >= cx.n_pad) return;
+    int sl = cx.col_slot[p];
+    float u = cx.utab[j * cx.n_slot + sl];
+    float cr = cx.c_slot[sl] * cx.inv_rho[j];
+    float q = cx.q1[(size_t)j * cx.n_pad + p];
+    float z = fminf(fmaxf(q, 0.f), u);
+    float r = 2.f * z - q - cr;
+    size_t o = (size_t)j * cx.n_pad + p;
+    if (BF16) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(r, hi, lo);
+        static_cast<__nv_bfloat16*>(R1)[o] = hi;
+        static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
+    } else {
+        static_cast<float*>(R1)[o] = r;
+    }
+}
+
+// rhs = sum_s part[s] + q2 - 2 P2(q2)
+template <bool BF16>
+__global__ void k_reduce_rhs(IterCtx cx, const float* __restrict__ part, int splits, void* rhs) {
+    if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= cx.m_pad) return;
+    size_t o = (size_t)j * cx.m_pad + i;
+    float acc = 0.f;
+    for (int s = 0; s < splits; ++s) acc += part[(size_t)s * cx.Kp * cx.m_pad + o];
+    float q = cx.q2[o];
+    float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
+    float r = acc + q - 2.f * p2;
+    if (BF16) {      // three BF16 parts: the solve amplifies input rounding
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(rhs);
+        const size_t plane = (size_t)cx.Kp * cx.m_pad;
+        __nv_bfloat16 hi = __float2bfloat16_rn(r);
+        float r1 = r - __bfloat162float(hi);
+        __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        d[o] = hi;
+        d[plane + o] = mid;
+        d[2 * plane + o] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    } else {
+        static_cast<float*>(rhs)[o] = r;
+    }
+}
+
+// v = sum_s part[s];  q2' = v + P2(q2);  residual partials of the m-block.
+template <bool BF16>
+__global__ void k_reduce_solve(IterCtx cx, const float* __restrict__ part, int splits, void* V) {
+    if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
+    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < cx.m_pad) {
+        size_t o = (size_t)j * cx.m_pad + i;
+        float v = 0.f;
+        for (int s = 0; s < splits; ++s) v += part[(size_t)s * cx.Kp * cx.m_pad + o];
+        float qo = cx.q2[o];
+        float bb = b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
+        float zo = fminf(qo, bb);
+        float qn = v + zo;
+        if (cx.active[j]) cx.q2[o] = qn;
+        if (BF16) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(v, hi, lo);
+            static_cast<__nv_bfloat16*>(V)[o] = hi;
+            static_cast<__nv_bfloat16*>(V)[(size_t)cx.Kp * cx.m_pad + o] = lo;
+        } else {
+            static_cast<float*>(V)[o] = v;
+        }
+        if (check) {
+            float yo = qo - zo, zn = fminf(qn, bb), yn = qn - zn;
+            float r = yn - yo, x = qn - yo, s = zn - zo;
+            res[0] = r * r; res[1] = x * x; res[2] = zn * zn; res[3] = s * s; res[4] = yn * yn;
+        }
+    }
+    if (check) {
+        __shared__ double out[5];
+        block_sum5(res, out);
+        if (threadIdx.x == 0) {
+            double* dst = cx.resid + ((size_t)(cx.n_resid_n + blockIdx.x) * cx.Kp + j) * 5;
+            for (int k = 0; k < 5; ++k) dst[k] = out[k];
+        }
+    }
+}
+
+// FP32 path: q1' = P1(q1) - c/rho - W and R1' from W = A^T V (cuBLAS output).
+__global__ void k_gemm2_ep_f32(IterCtx cx, const float* __restrict__ W, float* __restrict__ R1) {
+    if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
+    int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
+    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (p < cx.n_pad) {
+        size_t o = (size_t)j * cx.n_pad + p;
+        int sl = cx.col_slot[p];
+        float u = cx.utab[j * cx.n_slot + sl];
+        float cr = cx.c_slot[sl] * cx.inv_rho[j];
+        Q1Update q = q1_update(cx.q1[o], W[o], u, cr);
+        if (cx.active[j]) cx.q1[o] = q.qn;
+        R1[o] = q.r1;
+        if (check)
+            for (int k = 0; k < 5; ++k) res[k] = q.res[k];
+    }
+    if (check) {
+        __shared__ double out[5];
+        block_sum5(res, out);
+        if (threadIdx.x == 0) {
+            double* dst = cx.resid + ((size_t)blockIdx.x * cx.Kp + j) * 5;
+            for (int k = 0; k < 5; ++k) dst[k] = out[k];
+        }
+    }
+}
+
+// Per-column stop test and bookkeeping; the last kernel of every iteration.
+__global__ void k_finalize(IterCtx cx) {
+    Control* c = cx.ctrl;
+    if (c->n_active == 0) return;
+    if (c->err) {           // a device error stops every column
+        for (int j = threadIdx.x; j < cx.Kp; j += blockDim.x) cx.active[j] = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) c->n_active = 0;
+        return;
+    }
+    int it = c->iter + 1;
+    bool check = (cx.tol > 0.f && it % cx.check_every == 0) || it >= c->max_iter;
+    bool test = cx.tol > 0.f && it % cx.check_every == 0;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int nb = cx.n_resid_n + cx.n_resid_m;
+    double sq = sqrt((double)(cx.n + cx.m_rows));
+    for (int j = threadIdx.x; j < cx.Kp; j += blockDim.x) {
+        int* act = cx.active;
+        if (!act[j]) continue;
+        cx.iters[j] = it;
+        bool stop = it >= c->max_iter;
+        if (check) {
+            double s5[5] = {0, 0, 0, 0, 0};
+            for (int b = 0; b < nb; ++b)
+                for (int k = 0; k < 5; ++k) s5[k] += cx.resid[((size_t)b * cx.Kp + j) * 5 + k];
+            double rho = cx.rho[j];
+            double rn = sqrt(s5[0]), xn = sqrt(s5[1]), zn = sqrt(s5[2]);
+            double sn = rho * sqrt(s5[3]), yn = rho * sqrt(s5[4]);
+            double xz = fmax(xn, zn);
+            cx.stats[j] = rn / fmax(xz, 1e-300);
+            cx.stats[cx.Kp + j] = sn / fmax(yn, 1e-300);
+            if (test && rn <= cx.eps_abs * sq + cx.tol * xz && sn <= cx.eps_abs * sq + cx.tol * yn) {
+                stop = true;
+                act[cx.Kp + j] = 1;   // converged
+            }
+        }
+        if (stop) act[j] = 0;
+        else atomicAdd(&cnt, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        c->n_active = cnt;
+        c->iter = it;
+    }
+}
+
+// c^T z1 in FP64 per column (deterministic block reduction).
+__global__ void k_objective(IterCtx cx, double* obj) {
+    int j = blockIdx.x;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int p = threadIdx.x; p < cx.n_pad; p += 256) {
+        int sl = cx.col_slot[p];
+        float u = cx.utab[j * cx.n_slot + sl];
+        float z = fminf(fmaxf(cx.q1[(size_t)j * cx.n_pad + p], 0.f), u);
+        s += (double)cx.c_slot[sl] * (double)z;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) obj[j] = red[0];
+}
+
+// lambda = D_r * rho * y2 = D_r * rho * max(q2 - b, 0) (FP64), K x m.
+__global__ void k_lambda(IterCtx cx, int K, double* lam) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= cx.m || j >= K) return;
+    double q = cx.q2[(size_t)j * cx.m_pad + i];
+    double bb = (double)b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
+    lam[(size_t)j * cx.m + i] = cx.Dr[i] * (double)cx.rho[j] * fmax(q - bb, 0.0);
+}
+
+// q1 (K x n) and q2 (K x m) of the q-form state, FP64.
+__global__ void k_state(IterCtx cx, int K, double* q1, double* q2) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (j >= K) return;
+    if (q1 && e < cx.n) q1[(size_t)j * cx.n + e] = cx.q1[(size_t)j * cx.n_pad + e];
+    if (q2 && e < cx.m) q2[(size_t)j * cx.m + e] = cx.q2[(size_t)j * cx.m_pad + e];
+}
+
+// ----------------------------------------------------------------- driver
+
+static IterCtx make_ctx(ResultData& r) {
+    CaseData& cs = *r.cs;
+    IterCtx cx{};
+    cx.Kp = r.Kp; cx.m = cs.m; cx.m_pad = cs.m_pad; cx.n_pad = cs.n_pad; cx.n_beams = cs.n_beams;
+    cx.n_slot = cs.n_slot; cx.check_every = cs.prm.check_every; cx.max_iter = r.max_iter;
+    cx.tol = (float)r.tol;
+    cx.col_slot = cs.col_slot.as<uint8_t>();
+    cx.utab = r.utab.as<float>();
+    cx.c_slot = r.utab.as<float>() + (size_t)r.Kp * cs.n_slot;
+    cx.rho = r.colp.as<float>();
+    cx.inv_rho = r.colp.as<float>() + r.Kp;
+    cx.wbot = r.colp.as<float>() + 2 * r.Kp;
+    cx.Dr = cs.Dr.as<double>();
+    cx.q1 = r.q1.as<float>(); cx.q2 = r.q2.as<float>();
+    cx.active = r.active.as<int>(); cx.iters = r.iters.as<int>();
+    cx.ctrl = r.ctrl.as<Control>();
+    cx.resid = r.resid.as<double>();
+    cx.stats = r.stats.as<double>();
+    cx.n_resid_n = r.n_resid_n; cx.n_resid_m = r.n_resid_m;
+    cx.eps_abs = cs.prm.eps_abs;
+    cx.n = cs.n; cx.m_rows = cs.m;
+    return cx;
+}
+
+IterCtx make_ctx_public(ResultData& r) { return make_ctx(r); }
+
+static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
+    CaseData& cs = *r.cs;
+    cudaStream_t st = cs.stream;
+    const float one = 1.f, zero = 0.f;
+    float* part = r.part.as<float>();
+    prof_mark(r, itx, 0);
+    // GEMM1: part[Kp][m_pad] = R1[Kp][n_pad] . A[m_pad][n_pad]^T
+    if (cublasSgemm(cs.cublas, CUBLAS_OP_T, CUBLAS_OP_N, cs.m_pad, r.Kp, cs.n_pad, &one,
+                    cs.A32.as<float>(), cs.n_pad, r.R1.as<float>(), cs.n_pad, &zero, part,
+                    cs.m_pad) != CUBLAS_STATUS_SUCCESS) {
+        set_error("cublasSgemm (GEMM1) failed");
+        return LGK_ECUDA;
+    }
+    count_launch();
+    prof_mark(r, itx, 1);
+    dim3 gm((cs.m_pad + 255) / 256, r.Kp);
+    k_reduce_rhs<false><<<gm, 256, 0, st>>>(cx, part, 1, r.rhs.p);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 2);
+    // solve: part = rhs . G^T (G symmetric)
+    if (cublasSgemm(cs.cublas, CUBLAS_OP_T, CUBLAS_OP_N, cs.m_pad, r.Kp, cs.m_pad, &one,
+                    cs.G32.as<float>(), cs.m_pad, r.rhs.as<float>(), cs.m_pad, &zero, part,
+                    cs.m_pad) != CUBLAS_STATUS_SUCCESS) {
+        set_error("cublasSgemm (solve) failed");
+        return LGK_ECUDA;
+    }
+    count_launch();
+    prof_mark(r, itx, 3);
+    k_reduce_solve<false><<<gm, 256, 0, st>>>(cx, part, 1, r.V.p);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 4);
+    // GEMM2: W[Kp][n_pad] = V[Kp][m_pad] . A[m_pad][n_pad]
+    if (cublasSgemm(cs.cublas, CUBLAS_OP_N, CUBLAS_OP_N, cs.n_pad, r.Kp, cs.m_pad, &one,
+                    cs.A32.as<float>(), cs.n_pad, r.V.as<float>(), cs.m_pad, &zero,
+                    r.W.as<float>(), cs.n_pad) != CUBLAS_STATUS_SUCCESS) {
+        set_error("cublasSgemm (GEMM2) failed");
+        return LGK_ECUDA;
+    }
+    count_launch();
+    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
+    k_gemm2_ep_f32<<<gn, 256, 0, st>>>(cx, r.W.as<float>(), r.R1.as<float>());
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 5);
+    k_finalize<<<1, 1024, 0, st>>>(cx);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 6);
+    return LGK_OK;
+}
+
+static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
+    CaseData& cs = *r.cs;
+    cudaStream_t st = cs.stream;
+    int rc;
+    prof_mark(r, itx, 0);
+    if ((rc = tc_gemm1(r))) return rc;
+    prof_mark(r, itx, 1);
+    dim3 gm((cs.m_pad + 255) / 256, r.Kp);
+    k_reduce_rhs<true><<<gm, 256, 0, st>>>(cx, r.part.as<float>(), r.splits1, r.rhs.p);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 2);
+    if ((rc = tc_solve(r))) return rc;
+    prof_mark(r, itx, 3);
+    k_reduce_solve<true><<<gm, 256, 0, st>>>(cx, r.part.as<float>(), r.splits_s, r.V.p);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 4);
+    if ((rc = tc_gemm2(r))) return rc;
+    prof_mark(r, itx, 5);
+    k_finalize<<<1, 1024, 0, st>>>(cx);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 6);
+    return LGK_OK;
+}
+
+int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
+              const double* q2_init) {
+    CaseData& cs = *r.cs;
+    cudaStream_t st = cs.stream;
+    const bool bf16 = cs.prm.precision != LGK_PREC_FP32;
+    const int K = r.K;
+    // column tiles: <= 256 columns each, multiples of 16 (tcgen05 N)
+    int kp16 = (int)round_up(K, 16);
+    int nt = (kp16 + 255) / 256;
+    r.n_tile = (int)round_up((kp16 + nt - 1) / nt, 16);
+    if (r.n_tile > 128) r.n_tile = (int)round_up(r.n_tile, 32);
+    r.Kp = r.n_tile * nt;
+    // the solve carries three B parts per stage: halve wide tiles
+    r.n_tile_s = r.n_tile > 128 ? r.n_tile / 2 : r.n_tile;
+    const int Kp = r.Kp, T = cs.n_targets, S = cs.n_slot;
+
+    // per-column tables (Appendix A bounds; Eq. rho_rule or caller rho)
+    std::vector<float> utab((size_t)Kp * S + S, 0.0f), colp((size_t)4 * Kp, 0.0f);
+    for (int j = 0; j < K; ++j) {
+        double wT = W[4 * j], wR = W[4 * j + 1], wLD = W[4 * j + 2], wB = W[4 * j + 3];
+        float* u = &utab[(size_t)j * S];
+        for (int k = 0; k < T; ++k) {
+            u[3 * k] = cs.slot_count[3 * k] ? (float)(cs.q_area[k] * wT / cs.slot_count[3 * k]) : 0.f;
+            u[3 * k + 1] = cs.slot_count[3 * k + 1] ? (float)(cs.q_vol[k] * wT / cs.slot_count[3 * k + 1]) : 0.f;
+            u[3 * k + 2] = cs.slot_count[3 * k + 2] ? (float)((wR / T) / cs.slot_count[3 * k + 2]) : 0.f;
+        }
+        u[slot_ld1(T)] = cs.slot_count[slot_ld1(T)] ? (float)(wLD / cs.slot_count[slot_ld1(T)]) : 0.f;
+        u[slot_ld2(T)] = cs.slot_count[slot_ld2(T)] ? (float)(wLD / cs.slot_count[slot_ld2(T)]) : 0.f;
+        u[slot_oar(T)] = INFINITY;
+        u[slot_bot(T)] = INFINITY;
+        u[slot_pad(T)] = 0.f;
+        colp[j] = (float)rho[j];
+        colp[Kp + j] = (float)(1.0 / rho[j]);
+        colp[2 * Kp + j] = (float)wB;
+    }
+    for (int s = 0; s < S; ++s) utab[(size_t)Kp * S + s] = cs.c_of_slot[s];
+
+    // buffers
+    int rc;
+    const size_t nq = (size_t)Kp * cs.n_pad, mq = (size_t)Kp * cs.m_pad;
+    if ((rc = r.q1.alloc(nq * 4)) || (rc = r.q2.alloc(mq * 4))) return rc;
+    if ((rc = r.R1.alloc(bf16 ? nq * 4 : nq * 4))) return rc;     // 2 x bf16 or 1 x f32
+    if ((rc = r.rhs.alloc(bf16 ? mq * 6 : mq * 4)) || (rc = r.V.alloc(mq * 4))) return rc;
+    if (!bf16 && (rc = r.W.alloc(nq * 4))) return rc;
+    int row_tiles_m = cs.m_pad / 128, n_tiles = Kp / r.n_tile;
+    if (bf16) {
+        r.splits1 = plan_splits(cs.n_pad / 64, row_tiles_m, n_tiles);
+        r.splits_s = plan_splits(cs.m_pad / 64, row_tiles_m, r.Kp / r.n_tile_s);
+    } else {
+        r.splits1 = r.splits_s = 1;
+    }
+    int max_split = std::max(r.splits1, r.splits_s);
+    if ((rc = r.part.alloc((size_t)max_split * mq * 4))) return rc;
+    if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
+    if ((rc = r.active.alloc((size_t)2 * Kp * 4)) || (rc = r.iters.alloc((size_t)Kp * 4))) return rc;
+    if ((rc = r.ctrl.alloc(sizeof(Control)))) return rc;
+    r.n_resid_n = bf16 ? cs.n_pad / 128 : (cs.n_pad + 255) / 256;
+    r.n_resid_m = (cs.m_pad + 255) / 256;
+    if ((rc = r.resid.alloc((size_t)(r.n_resid_n + r.n_resid_m) * Kp * 5 * 8))) return rc;
+    if ((rc = r.stats.alloc((size_t)3 * Kp * 8))) return rc;
+
+    std::vector<int> act(2 * Kp, 0);
+    for (int j = 0; j < K; ++j) act[j] = 1;
+    Control c0{0, K, r.max_iter, 0};
+    LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(r.active.p, act.data(), act.size() * 4, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(r.ctrl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(r.iters.p, 0, r.iters.bytes, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(r.q1.p, 0, r.q1.bytes, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(r.q2.p, 0, r.q2.bytes, st));
+    std::vector<float> init_buf;
+    if (q1_init) {       // warm start / resume: K x n FP64 -> [Kp][n_pad] FP32
+        init_buf.assign((size_t)Kp * cs.n_pad, 0.0f);
+        for (int j = 0; j < K; ++j)
+            for (int p = 0; p < cs.n; ++p) init_buf[(size_t)j * cs.n_pad + p] = (float)q1_init[(size_t)j * cs.n + p];
+        LGK_CUDA_TRY(cudaMemcpyAsync(r.q1.p, init_buf.data(), init_buf.size() * 4, cudaMemcpyHostToDevice, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (q2_init) {
+        init_buf.assign((size_t)Kp * cs.m_pad, 0.0f);
+        for (int j = 0; j < K; ++j)
+            for (int i = 0; i < cs.m; ++i) init_buf[(size_t)j * cs.m_pad + i] = (float)q2_init[(size_t)j * cs.m + i];
+        LGK_CUDA_TRY(cudaMemcpyAsync(r.q2.p, init_buf.data(), init_buf.size() * 4, cudaMemcpyHostToDevice, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    LGK_CUDA_TRY(cudaMemsetAsync(r.stats.p, 0, r.stats.bytes, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(r.resid.p, 0, r.resid.bytes, st));
+
+    IterCtx cx = make_ctx(r);
+    {
+        dim3 g((cs.n_pad + 255) / 256, Kp);
+        if (bf16) k_init_r1<true><<<g, 256, 0, st>>>(cx, r.R1.p);
+        else k_init_r1<false><<<g, 256, 0, st>>>(cx, r.R1.p);
+        LGK_LAUNCH_CHECK();
+    }
+    if (bf16) {
+        if ((rc = tc_prepare(r))) return rc;
+    } else {
+        cublasSetStream(cs.cublas, st);
+    }
+
+    // capture a CUDA graph of `per_graph` iterations, replay until done
+    int per_graph = std::max(1, std::min(r.max_iter, 5 * cs.prm.check_every));
+    cudaGraph_t g = nullptr;
+    if (cs.prm.profile) {
+        r.prof_ev.assign((size_t)per_graph * 7, nullptr);
+        for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
+    }
+    LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    long long before = 0;
+    (void)before;
+    for (int it = 0; it < per_graph; ++it) {
+        rc = bf16 ? iteration_bf16(r, cx, it) : iteration_fp32(r, cx, it);
+        if (rc) {
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+    }
+    LGK_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    cudaError_t e = cudaGraphInstantiate(&r.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        return LGK_ECUDA;
+    }
+    r.graph_iters = per_graph;
+    size_t n_nodes = 0;
+    {
+        // kernels per iteration: 6 (both precisions)
+        n_nodes = (size_t)per_graph * 6;
+    }
+
+    Control* hc = nullptr;
+    LGK_CUDA_TRY(cudaMallocHost(&hc, sizeof(Control)));
+    int iter_before = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    rc = LGK_OK;
+    for (;;) {
+        cudaError_t le = cudaGraphLaunch(r.graph, st);
+        if (le != cudaSuccess) { set_error(cudaGetErrorString(le)); rc = LGK_ECUDA; break; }
+        count_launch((long long)n_nodes - 0);
+        cudaMemcpyAsync(hc, r.ctrl.p, sizeof(Control), cudaMemcpyDeviceToHost, st);
+        for (;;) {
+            cudaError_t q = cudaStreamQuery(st);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) { set_error(cudaGetErrorString(q)); rc = LGK_ECUDA; break; }
+            auto el = std::chrono::steady_clock::now() - t0;
+            if (std::chrono::duration_cast<std::chrono::milliseconds>(el).count() > cs.prm.timeout_ms) {
+                set_error("solve exceeded timeout_ms");
+                rc = LGK_ETIMEOUT;
+                break;
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        if (rc) break;
+        if (hc->err) {
+            set_error("device error flag " + std::to_string(hc->err) + " raised during the solve");
+            rc = LGK_ECUDA;
+            break;
+        }
+        if (!r.prof_ev.empty()) {       // iterations of this replay that did work
+            int worked = std::min(per_graph, hc->iter - iter_before);
+            for (int it = 0; it < worked; ++it)
+                for (int k = 0; k < LGK_K_COUNT; ++k) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, r.prof_ev[(size_t)it * 7 + k],
+                                             r.prof_ev[(size_t)it * 7 + k + 1]) == cudaSuccess) {
+                        r.prof_ms[k] += ms;
+                        r.prof_n[k] += 1;
+                    } else {
+                        cudaGetLastError();      // not sticky; keep it out of later checks
+                    }
+                }
+        }
+        iter_before = hc->iter;
+        if (hc->n_active == 0) break;
+    }
+    cudaFreeHost(hc);
+    if (rc) return rc;
+    k_objective<<<Kp, 256, 0, st>>>(cx, r.stats.as<double>() + 2 * Kp);
+    LGK_LAUNCH_CHECK();
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    return LGK_OK;
+}
+
+// ------------------------------------------------------------------ fetch
+
+int fetch_times(const ResultData& r, double* t, double* tau) {
+    ResultData& rr = const_cast<ResultData&>(r);
+    CaseData& cs = *rr.cs;
+    cudaStream_t st = cs.stream;
+    DevBuf lam;
+    int rc;
+    if ((rc = lam.alloc((size_t)r.K * cs.m * 8))) return rc;
+    IterCtx cx = make_ctx(rr);
+    dim3 g((cs.m + 255) / 256, r.K);
+    k_lambda<<<g, 256, 0, st>>>(cx, r.K, lam.as<double>());
+    LGK_LAUNCH_CHECK();
+    std::vector<double> h((size_t)r.K * cs.m);
+    LGK_CUDA_TRY(cudaMemcpyAsync(h.data(), lam.p, h.size() * 8, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < r.K; ++j) {
+        if (t) std::copy(&h[(size_t)j * cs.m], &h[(size_t)j * cs.m + cs.n_beams], t + (size_t)j * cs.n_beams);
+        if (tau)
+            std::copy(&h[(size_t)j * cs.m + cs.n_beams], &h[(size_t)j * cs.m + cs.m],
+                      tau + (size_t)j * cs.n_iso);
+    }
+    return LGK_OK;
+}
+
+int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double* dose) {
+    ResultData& rr = const_cast<ResultData&>(r);
+    CaseData& cs = *rr.cs;
+    cudaStream_t st = cs.stream;
+    const int B = cs.n_beams, K = r.K;
+    std::vector<double> t((size_t)K * B);
+    int rc;
+    if ((rc = fetch_times(r, t.data(), nullptr))) return rc;
+    DevBuf td, pd, dd;
+    if ((rc = td.alloc(t.size() * 8)) || (rc = pd.alloc((size_t)n_eval * B * 8)) ||
+        (rc = dd.alloc((size_t)K * n_eval * 8)))
+        return rc;
+    LGK_CUDA_TRY(cudaMemcpyAsync(td.p, t.data(), td.bytes, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(pd.p, phi_eval, pd.bytes, cudaMemcpyHostToDevice, st));
+    // dose[K][E] = t[K][B] . phi_eval[E][B]^T
+    if ((rc = dgemm(st, false, true, K, n_eval, B, 1.0, td.as<double>(), B, pd.as<double>(), B, 0.0,
+                    dd.as<double>(), n_eval)))
+        return rc;
+    LGK_CUDA_TRY(cudaMemcpyAsync(dose, dd.p, dd.bytes, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    return LGK_OK;
+}
+
+int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri, double* rel_dual,
+                uint8_t* converged) {
+    CaseData& cs = *r.cs;
+    cudaStream_t st = cs.stream;
+    const int K = r.K, Kp = r.Kp;
+    std::vector<int> it(Kp), act(2 * Kp);
+    std::vector<double> stv(3 * Kp);
+    LGK_CUDA_TRY(cudaMemcpyAsync(it.data(), r.iters.p, Kp * 4, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(act.data(), r.active.p, 2 * Kp * 4, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(stv.data(), r.stats.p, 3 * Kp * 8, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int j = 0; j < K; ++j) {
+        if (iters) iters[j] = it[j];
+        if (rel_pri) rel_pri[j] = stv[j];
+        if (rel_dual) rel_dual[j] = stv[Kp + j];
+        if (obj) obj[j] = stv[2 * Kp + j];
+        if (converged) converged[j] = (uint8_t)act[Kp + j];
+    }
+    return LGK_OK;
+}
+
+int fetch_state(const ResultData& r, double* q1, double* q2) {
+    ResultData& rr = const_cast<ResultData&>(r);
+    CaseData& cs = *rr.cs;
+    cudaStream_t st = cs.stream;
+    DevBuf zd, yd;
+    int rc;
+    if ((rc = zd.alloc((size_t)r.K * cs.n * 8)) || (rc = yd.alloc((size_t)r.K * cs.m * 8))) return rc;
+    IterCtx cx = make_ctx(rr);
+    int ne = std::max(cs.n, cs.m);
+    dim3 g((ne + 255) / 256, r.K);
+    k_state<<<g, 256, 0, st>>>(cx, r.K, zd.as<double>(), yd.as<double>());
+    LGK_LAUNCH_CHECK();
+    if (q1) LGK_CUDA_TRY(cudaMemcpyAsync(q1, zd.p, zd.bytes, cudaMemcpyDeviceToHost, st));
+    if (q2) LGK_CUDA_TRY(cudaMemcpyAsync(q2, yd.p, yd.bytes, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    return LGK_OK;
+}
+
+}  // namespace lgk

@@ -1,0 +1,95 @@
+// Internal definitions shared by the liblgk translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lgk.h"
+
+namespace lgk {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void count_launch(long long n = 1);
+
+struct Status {
+    int code = LGK_OK;
+};
+
+#define LGK_CUDA_TRY(expr)                                                      \
+    do {                                                                        \
+        cudaError_t _e = (expr);                                                \
+        if (_e != cudaSuccess) {                                                \
+            ::lgk::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e) \
+                             + " (" + __FILE__ + ":" + std::to_string(__LINE__) \
+                             + ")");                                            \
+            return _e == cudaErrorMemoryAllocation ? LGK_ENOMEM : LGK_ECUDA;    \
+        }                                                                       \
+    } while (0)
+
+#define LGK_LAUNCH_CHECK()                                                      \
+    do {                                                                        \
+        ::lgk::count_launch();                                                  \
+        cudaError_t _e = cudaGetLastError();                                    \
+        if (_e != cudaSuccess) {                                                \
+            ::lgk::set_error(std::string("kernel launch: ") +                   \
+                             cudaGetErrorString(_e) + " (" + __FILE__ + ":" +   \
+                             std::to_string(__LINE__) + ")");                   \
+            return LGK_ECUDA;                                                   \
+        }                                                                       \
+    } while (0)
+
+// ------------------------------------------------------------ small helpers
+__host__ __device__ inline long long round_up(long long x, long long r) {
+    return (x + r - 1) / r * r;
+}
+
+// Device-side error codes written into Control::err.
+enum DeviceError : int {
+    DERR_NONE = 0,
+    DERR_MBAR_TIMEOUT = 1,   // a bounded mbarrier wait in a tensor-core GEMM ran out
+    DERR_NOT_PD = 2,         // non-positive pivot in the FP64 Cholesky
+    DERR_BAD_SHAPE = 3,      // a kernel was launched with a shape it cannot handle
+};
+
+// Control block of one solve (device memory).
+struct Control {
+    int iter;        // iterations completed
+    int n_active;    // columns still iterating
+    int max_iter;
+    int err;         // DeviceError
+};
+
+// Point-class slots of the A columns: per target k: TS=3k, TI=3k+1, R=3k+2;
+// then LD1, LD2, OAR, BOT (coupling columns), PAD (zero padding).
+__host__ __device__ inline int slot_ld1(int n_targets) { return 3 * n_targets; }
+__host__ __device__ inline int slot_ld2(int n_targets) { return 3 * n_targets + 1; }
+__host__ __device__ inline int slot_oar(int n_targets) { return 3 * n_targets + 2; }
+__host__ __device__ inline int slot_bot(int n_targets) { return 3 * n_targets + 3; }
+__host__ __device__ inline int slot_pad(int n_targets) { return 3 * n_targets + 4; }
+__host__ __device__ inline int n_slots(int n_targets) { return 3 * n_targets + 5; }
+constexpr int kMaxTargets = 64;      // keeps slot ids below 255
+
+// Exact round-to-nearest-even of an FP64 value to bfloat16 (8 significant
+// bits, FP32 exponent range, subnormal spacing 2^-133): scale to an integer
+// significand, round with rint (ties to even), scale back.  The result has at
+// most 8 significant bits and lies in float range, so the float conversion and
+// the final bf16 conversion are exact.
+__device__ inline __nv_bfloat16 bf16_from_double(double x) {
+    if (x == 0.0 || !isfinite(x)) return __float2bfloat16_rn((float)x);
+    double ax = fabs(x);
+    int e;
+    frexp(ax, &e);           // ax = f 2^e, f in [0.5, 1)
+    e -= 1;                  // ax in [2^e, 2^(e+1))
+    if (e < -126) e = -126;
+    double q = ldexp(1.0, e - 7);
+    double r = rint(ax / q) * q;
+    float rf = r >= 0x1p128 ? __int_as_float(0x7f800000) : (float)r;
+    return __float2bfloat16_rn(x < 0 ? -rf : rf);
+}
+
+}  // namespace lgk

@@ -1,0 +1,118 @@
+// Host-side objects behind the opaque lgk_case / lgk_result handles.
+#pragma once
+
+#include <cublas_v2.h>
+
+#include <memory>
+#include <vector>
+
+#include "lgk_common.cuh"
+
+namespace lgk {
+
+// Device buffer owned by a case or result.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { if (p) cudaFree(p); }
+    int alloc(size_t n);
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct CaseData {
+    lgk_params prm{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cublasHandle_t cublas = nullptr;
+    DevBuf cublas_ws;
+
+    // problem sizes (Appendix A): m = 24N + N rows, n = P + 8N columns
+    int n_iso = 0, n_pts = 0, n_beams = 0, m = 0, n = 0;
+    int m_pad = 0, n_pad = 0;              // multiples of 128
+    int n_targets = 0, n_oars = 0, n_slot = 0;
+    double beta = 1.0;
+    std::vector<int> slot_count;           // points per slot (TS/TI/R per target, LD1, LD2, OAR)
+    std::vector<double> q_area, q_vol;
+    std::vector<float> c_of_slot;          // c per slot (Appendix A: -1, -1, +1, +1, +1, 0)
+
+    DevBuf col_slot;   // uint8 [n_pad]
+    DevBuf Dr;         // double [m_pad] row scale D_r (1 on padding rows)
+    DevBuf A32;        // float [m_pad][n_pad]           (LGK_PREC_FP32)
+    DevBuf Ahat;       // bf16 [na][m_pad][n_pad]: A = hi (+ lo)   (BF16 forms)
+    int na = 0;        // BF16 terms of A: 1 (LGK_PREC_BF16), 2 (LGK_PREC_BF16X3)
+    DevBuf G32;        // float [m_pad][m_pad] S^{-1}    (LGK_PREC_FP32)
+    DevBuf G3;         // bf16 [3][m_pad][m_pad] S^{-1} = hi + mid + lo (BF16 forms)
+    DevBuf ctrl_setup; // int [4] device error flags during set-up
+    size_t bytes_held() const;
+    ~CaseData();
+};
+
+// TMA descriptors of one solve's operands (128B-swizzled BF16 tiles).
+struct TcMaps {
+    CUtensorMap A_k;    // A terms, K-major tiles 128 rows x 64 columns (GEMM1)
+    CUtensorMap A_mn;   // A terms, tiles 64 rows x 64 columns read MN-major (GEMM2)
+    CUtensorMap G3;     // S^{-1} hi/mid/lo, 128 x 64 tiles (solve)
+    CUtensorMap R1, rhs, V;   // hi/lo iterates, n_tile x 64 tiles
+};
+
+struct ResultData {
+    std::shared_ptr<CaseData> cs;
+    TcMaps maps;
+    bool maps_ready = false;
+    int K = 0, Kp = 0, n_tile = 0, n_tile_s = 0;   // column tiles: GEMMs, solve
+    double tol = 0.0;
+    int max_iter = 0;
+    int splits1 = 1, splits_s = 1;         // split-K factors of GEMM1 and the solve
+
+    DevBuf q1, q2;            // float [Kp][n_pad], [Kp][m_pad]
+    DevBuf R1;                // FP32: float [Kp][n_pad]; BF16: bf16 [2][Kp][n_pad]
+    DevBuf rhs, V;            // FP32: float [Kp][m_pad]; BF16: rhs bf16 [3][Kp][m_pad], V [2][Kp][m_pad]
+    DevBuf W;                 // FP32 only: float [Kp][n_pad] (A^T V before its epilogue)
+    DevBuf part;              // float [splits][Kp][m_pad] split-K partial sums
+    DevBuf utab;              // float [Kp][n_slot] upper bounds u per slot
+    DevBuf colp;              // float [4][Kp]: rho, 1/rho, w_BOT, unused
+    DevBuf active, iters;     // int [Kp]
+    DevBuf ctrl;              // Control
+    DevBuf resid;             // double [n_resid_blocks][Kp][5] residual partial sums
+    DevBuf stats;             // double [3][Kp]: rel_pri, rel_dual, obj
+    int n_resid_n = 0, n_resid_m = 0;     // residual partial blocks from the n- and m-blocks
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    std::vector<cudaEvent_t> prof_ev;        // 7 per captured iteration (kernel boundaries)
+    double prof_ms[LGK_K_COUNT] = {0};
+    long long prof_n[LGK_K_COUNT] = {0};
+    ~ResultData();
+};
+
+// set-up (setup.cu)
+int setup_case(CaseData& cs, const lgk_case_desc& d);
+
+// one solve (iter.cu)
+int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
+              const double* q2_init);
+int fetch_times(const ResultData& r, double* t, double* tau);
+int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double* dose);
+int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri,
+                double* rel_dual, uint8_t* converged);
+int fetch_state(const ResultData& r, double* q1, double* q2);
+
+// FP64 GEMM (setup.cu):  C = alpha op(A) op(B) + beta C, row-major.
+int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
+          const double* A, int lda, const double* B, int ldb, double beta,
+          double* C, int ldc);
+
+// Tensor-core GEMMs (tc_gemm.cu)
+int plan_splits(int kblocks, int row_tiles, int n_tiles);
+struct IterCtx;
+IterCtx make_ctx_public(ResultData& r);
+int tc_prepare(ResultData& r);  // attributes + TMA maps, before capture
+int tc_gemm1(ResultData& r);     // part[s] = Ahat . R1^T over split s of the columns
+int tc_solve(ResultData& r);     // part[s] = G3 . rhs^T  (5 products)
+int tc_gemm2(ResultData& r);     // fused: q1, R1 update from Ahat^T . V
+
+}  // namespace lgk

@@ -1,0 +1,504 @@
+// Case set-up on the device: dual-LP assembly (Appendix A), row and BOT-column
+// scaling (Sec. 3.C), rounding of A for the iterations, S = A A^T + I in FP64,
+// its FP64 Cholesky factor and the explicit inverse kept for the iterations
+// (Sec. 2.B caches a factorisation; Sec. 3.A keeps the explicit inverse).
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lgk_impl.hpp"
+
+namespace lgk {
+
+int DevBuf::alloc(size_t n) {
+    if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+    if (n == 0) return LGK_OK;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(" + std::to_string(n) + " bytes): " + cudaGetErrorString(e));
+        return LGK_ENOMEM;
+    }
+    bytes = n;
+    return LGK_OK;
+}
+
+size_t CaseData::bytes_held() const {
+    return col_slot.bytes + Dr.bytes + A32.bytes + Ahat.bytes + G32.bytes + G3.bytes +
+           cublas_ws.bytes + ctrl_setup.bytes;
+}
+
+// ------------------------------------------------------------- assembly
+
+// A[b][p] = sign_p phi[p][b] / D_p for point columns (32x32 tiled transpose).
+__global__ void k_assemble_points(const double* __restrict__ phi, const double* __restrict__ scale,
+                                  int P, int B, double* __restrict__ A, int lda) {
+    __shared__ double tile[32][33];
+    int p0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        int p = p0 + k, b = b0 + threadIdx.x;
+        tile[k][threadIdx.x] = (p < P && b < B) ? phi[(size_t)p * B + b] * scale[p] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        int b = b0 + k, p = p0 + threadIdx.x;
+        if (b < B && p < P) A[(size_t)b * lda + p] = tile[threadIdx.x][k];
+    }
+}
+
+// BOT columns p = P + (8 i + s): -C_S^T on beam rows (i, s, *), T^T on row B + i.
+__global__ void k_assemble_bot(int P, int n_iso, int B, double cs, double* __restrict__ A, int lda) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;     // (iso, sector) pair
+    if (q >= 8 * n_iso) return;
+    int col = P + q;
+    for (int c = 0; c < 3; ++c) A[(size_t)(3 * q + c) * lda + col] = -cs;
+    A[(size_t)(B + q / 8) * lda + col] = 1.0;
+}
+
+// D_r[i] = 1 / ||A[i, :]||_2 (1 for empty rows).  One block per row, fixed
+// reduction order (deterministic).
+__global__ void k_row_norm(const double* __restrict__ A, int lda, int ncols, int m,
+                           double* __restrict__ Dr) {
+    int i = blockIdx.x;
+    __shared__ double red[256];
+    double s = 0.0;
+    if (i < m)
+        for (int p = threadIdx.x; p < ncols; p += 256) {
+            double a = A[(size_t)i * lda + p];
+            s += a * a;
+        }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Dr[i] = (i < m && red[0] > 0.0) ? 1.0 / sqrt(red[0]) : 1.0;
+}
+
+// Scale rows by D_r and the BOT columns [P, n) by beta, round for the
+// iterations, and keep the rounded value in FP64 for S.  BF16 forms: NA terms
+// hi (+ lo), each the BF16 rounding of what the earlier terms leave, so
+// A = hi + lo holds exactly in FP64.
+template <int NA>
+__global__ void k_scale_round(double* __restrict__ A64, const double* __restrict__ Dr, int m_pad,
+                              int n_pad, int P, int n, double beta, void* __restrict__ out) {
+    size_t total = (size_t)m_pad * n_pad;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e / n_pad), p = (int)(e % n_pad);
+        double a = A64[e] * Dr[i];
+        if (p >= P && p < n) a *= beta;
+        if (NA > 0) {
+            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out);
+            __nv_bfloat16 h = bf16_from_double(a);
+            double kept = (double)__bfloat162float(h);
+            o[e] = h;
+            if (NA > 1) {
+                __nv_bfloat16 l = bf16_from_double(a - kept);
+                o[total + e] = l;
+                kept += (double)__bfloat162float(l);
+            }
+            A64[e] = kept;
+        } else {
+            float f = (float)a;
+            static_cast<float*>(out)[e] = f;
+            A64[e] = (double)f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- FP64 GEMM
+// C[M x N] = alpha op(A) op(B) + beta C; op(A) M x K (TA: A stored K x M),
+// op(B) K x N (TB: B stored N x K).  LOWER skips tiles above the diagonal.
+template <bool TA, bool TB, bool LOWER>
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha,
+                                               const double* __restrict__ A, int lda,
+                                               const double* __restrict__ B, int ldb,
+                                               double beta, double* __restrict__ C, int ldc) {
+    __shared__ double As[16][65];
+    __shared__ double Bs[16][65];
+    int tm = blockIdx.y, tn = blockIdx.x;
+    if (LOWER && tn > tm) return;
+    int m0 = tm * 64, n0 = tn * 64;
+    int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            int mm, kk;
+            if (TA) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
+            int gm = m0 + mm, gk = k0 + kk;
+            double v = 0.0;
+            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            As[kk][mm] = v;
+        }
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            int nn, kk;
+            if (TB) { nn = e >> 4; kk = e & 15; } else { kk = e >> 6; nn = e & 63; }
+            int gn = n0 + nn, gk = k0 + kk;
+            double v = 0.0;
+            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+            if (gm < M && gn < N) {
+                size_t o = (size_t)gm * ldc + gn;
+                C[o] = alpha * acc[i][j] + (beta != 0.0 ? beta * C[o] : 0.0);
+            }
+        }
+}
+
+int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+          int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+    if (M <= 0 || N <= 0) return LGK_OK;
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    if (!ta && !tb) k_dgemm<false, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (!ta && tb) k_dgemm<false, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else if (ta && !tb) k_dgemm<true, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else k_dgemm<true, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
+static int dgemm_lower_nt(cudaStream_t st, int M, int K, double alpha, const double* A, int lda,
+                          double beta, double* C, int ldc) {
+    if (M <= 0) return LGK_OK;
+    dim3 grid((M + 63) / 64, (M + 63) / 64);
+    k_dgemm<false, true, true><<<grid, 256, 0, st>>>(M, M, K, alpha, A, lda, A, lda, beta, C, ldc);
+    LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
+__global__ void k_add_identity(double* S, int ld, int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) S[(size_t)i * ld + i] += 1.0;
+}
+
+// ------------------------------------------------------------ FP64 Cholesky
+constexpr int NB = 64;
+
+// Factor the diagonal block at (k0, k0) in place: lower triangle <- L_kk.
+__global__ void k_potrf_diag(double* S, int ld, int k0, int* err) {
+    __shared__ double T[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        T[i][j] = S[(size_t)(k0 + i) * ld + k0 + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < NB; ++j) {
+        if (threadIdx.x == 0) {
+            double d = T[j][j];
+            if (!(d > 0.0)) { atomicExch(err, DERR_NOT_PD); d = 1.0; }
+            T[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < NB; i += blockDim.x) T[i][j] /= T[j][j];
+        __syncthreads();
+        int w = NB - 1 - j;     // trailing (i, k) with j < k <= i < NB
+        for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+            int i = j + 1 + e / w, k = j + 1 + e % w;
+            if (k <= i) T[i][k] -= T[i][j] * T[k][j];
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        S[(size_t)(k0 + i) * ld + k0 + j] = (j <= i) ? T[i][j] : 0.0;
+    }
+}
+
+// Rows r >= k0 + NB of the block column: L[r, k0:k0+NB] = S[r, k0:k0+NB] L_kk^{-T}.
+__global__ void k_trsm_panel(double* S, int ld, int k0, int M) {
+    __shared__ double Lk[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        Lk[i][j] = S[(size_t)(k0 + i) * ld + k0 + j];
+    }
+    __syncthreads();
+    int r = k0 + NB + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    double* row = S + (size_t)r * ld + k0;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = row[j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        double s = x[j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) s -= x[t] * Lk[j][t];
+        x[j] = s / Lk[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) row[j] = x[j];
+}
+
+// Zero the strict upper triangle (leaves L alone in the buffer).
+__global__ void k_zero_upper(double* S, int ld, int m) {
+    size_t total = (size_t)m * m;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e / m), j = (int)(e % m);
+        if (j > i) S[(size_t)i * ld + j] = 0.0;
+    }
+}
+
+__global__ void k_set_identity(double* Y, int ld, int m) {
+    size_t total = (size_t)m * m;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(e / m), j = (int)(e % m);
+        Y[(size_t)i * ld + j] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+// Y[k0:k0+NB, c] <- L_kk^{-1} Y[k0:k0+NB, c] for columns c < ncols.
+__global__ void k_trsm_rows(const double* L, int ldl, double* Y, int ldy, int k0, int ncols) {
+    __shared__ double Lk[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        Lk[i][j] = L[(size_t)(k0 + i) * ldl + k0 + j];
+    }
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = Y[(size_t)(k0 + j) * ldy + c];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        double s = x[j];
+#pragma unroll
+        for (int t = 0; t < j; ++t) s -= Lk[j][t] * x[t];
+        x[j] = s / Lk[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) Y[(size_t)(k0 + j) * ldy + c] = x[j];
+}
+
+// S^{-1} -> FP32, or -> three BF16 terms hi + mid + lo (each the bf16
+// rounding of what the previous terms leave).
+__global__ void k_inverse_out(const double* G, size_t total, float* g32, __nv_bfloat16* g3) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        double g = G[e];
+        if (g32) g32[e] = (float)g;
+        if (g3) {
+            __nv_bfloat16 h = bf16_from_double(g);
+            double r1 = g - (double)__bfloat162float(h);
+            __nv_bfloat16 mid = bf16_from_double(r1);
+            double r2 = r1 - (double)__bfloat162float(mid);
+            g3[e] = h;
+            g3[total + e] = mid;
+            g3[2 * total + e] = bf16_from_double(r2);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- set-up
+
+int setup_case(CaseData& cs, const lgk_case_desc& d) {
+    cudaStream_t st = cs.stream;
+    const int P = d.n_pts, N = d.n_iso, B = 24 * N;
+    const int m = B + N, n = P + 8 * N;
+    const int m_pad = (int)round_up(m, 128), n_pad = (int)round_up(n, 128);
+    const int T = d.n_targets;
+    cs.n_iso = N; cs.n_pts = P; cs.n_beams = B; cs.m = m; cs.n = n;
+    cs.m_pad = m_pad; cs.n_pad = n_pad;
+    cs.n_targets = T; cs.n_oars = d.n_oars; cs.n_slot = n_slots(T);
+    const bool bf16 = cs.prm.precision != LGK_PREC_FP32;
+    cs.na = cs.prm.precision == LGK_PREC_BF16X3 ? 2 : (bf16 ? 1 : 0);
+
+    // resident footprint check before any large allocation
+    size_t resident = (size_t)n_pad + (size_t)m_pad * 8 + 64 +
+                      (bf16 ? (size_t)cs.na * m_pad * n_pad * 2 + (size_t)3 * m_pad * m_pad * 2
+                            : (size_t)m_pad * n_pad * 4 + (size_t)m_pad * m_pad * 4);
+    if (cs.prm.hbm_budget && resident > cs.prm.hbm_budget) {
+        set_error("case footprint " + std::to_string(resident) + " B exceeds hbm_budget " +
+                  std::to_string(cs.prm.hbm_budget) + " B");
+        return LGK_EBUDGET;
+    }
+
+    // per-point slot, threshold and sign (Appendix A)
+    std::vector<uint8_t> slot(n_pad, (uint8_t)slot_pad(T));
+    std::vector<double> scale(P);
+    cs.slot_count.assign(cs.n_slot, 0);
+    double d_mean = 0.0;
+    for (int k = 0; k < T; ++k) d_mean += d.d_presc[k];
+    d_mean /= T;
+    for (int p = 0; p < P; ++p) {
+        int k = d.kind[p], s = d.struct_id[p];
+        int sl;
+        double D, sign;
+        switch (k) {
+            case LGK_TS: sl = 3 * s; D = d.d_presc[s]; sign = 1.0; break;
+            case LGK_TI: sl = 3 * s + 1; D = d.d_presc[s]; sign = 1.0; break;
+            case LGK_R: sl = 3 * s + 2; D = d.d_presc[s]; sign = -1.0; break;
+            case LGK_LD1: sl = slot_ld1(T); D = d.d_ld1; sign = -1.0; break;
+            case LGK_LD2: sl = slot_ld2(T); D = d.d_ld2; sign = -1.0; break;
+            default: sl = slot_oar(T); D = d.d_oar[s]; sign = -1.0; break;
+        }
+        slot[p] = (uint8_t)sl;
+        scale[p] = sign / D;
+        cs.slot_count[sl] += 1;
+    }
+    for (int q = P; q < n; ++q) slot[q] = (uint8_t)slot_bot(T);
+    cs.c_of_slot.assign(cs.n_slot, 0.0f);
+    for (int k = 0; k < T; ++k) {
+        cs.c_of_slot[3 * k] = -1.0f;
+        cs.c_of_slot[3 * k + 1] = -1.0f;
+        cs.c_of_slot[3 * k + 2] = 1.0f;
+    }
+    cs.c_of_slot[slot_ld1(T)] = 1.0f;
+    cs.c_of_slot[slot_ld2(T)] = 1.0f;
+    cs.c_of_slot[slot_oar(T)] = 1.0f;
+    cs.q_area.assign(d.q_area, d.q_area + T);
+    cs.q_vol.assign(d.q_vol, d.q_vol + T);
+    int n_cost = 0;
+    for (int p = 0; p < P; ++p) n_cost += d.kind[p] != LGK_OAR;
+    cs.beta = cs.prm.scale_bot ? n_cost / 2000.0 : 1.0;
+
+    int rc;
+    if ((rc = cs.col_slot.alloc(n_pad))) return rc;
+    if ((rc = cs.Dr.alloc((size_t)m_pad * 8))) return rc;
+    if ((rc = cs.ctrl_setup.alloc(16))) return rc;
+    LGK_CUDA_TRY(cudaMemcpyAsync(cs.col_slot.p, slot.data(), n_pad, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(cs.ctrl_setup.p, 0, 16, st));
+
+    // ---- A in FP64 (temporary)
+    DevBuf A64, phi_d, scale_d;
+    if ((rc = A64.alloc((size_t)m_pad * n_pad * 8))) return rc;
+    if ((rc = phi_d.alloc((size_t)P * B * 8))) return rc;
+    if ((rc = scale_d.alloc((size_t)P * 8))) return rc;
+    LGK_CUDA_TRY(cudaMemsetAsync(A64.p, 0, A64.bytes, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(phi_d.p, d.phi, phi_d.bytes, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(scale_d.p, scale.data(), scale_d.bytes, cudaMemcpyHostToDevice, st));
+    {
+        dim3 grid((P + 31) / 32, (B + 31) / 32), blk(32, 8);
+        k_assemble_points<<<grid, blk, 0, st>>>(phi_d.as<double>(), scale_d.as<double>(), P, B,
+                                                A64.as<double>(), n_pad);
+        LGK_LAUNCH_CHECK();
+        k_assemble_bot<<<(8 * N + 255) / 256, 256, 0, st>>>(P, N, B, d.phi_cal / d_mean,
+                                                            A64.as<double>(), n_pad);
+        LGK_LAUNCH_CHECK();
+    }
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    phi_d.alloc(0);
+    scale_d.alloc(0);
+
+    // ---- row norms, scaling, rounding (Sec. 3.C)
+    if (cs.prm.normalize_rows) {
+        k_row_norm<<<m_pad, 256, 0, st>>>(A64.as<double>(), n_pad, n_pad, m, cs.Dr.as<double>());
+        LGK_LAUNCH_CHECK();
+    } else {
+        std::vector<double> ones(m_pad, 1.0);
+        LGK_CUDA_TRY(cudaMemcpyAsync(cs.Dr.p, ones.data(), (size_t)m_pad * 8, cudaMemcpyHostToDevice, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (cs.na == 2) {
+        if ((rc = cs.Ahat.alloc((size_t)2 * m_pad * n_pad * 2))) return rc;
+        k_scale_round<2><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
+                                                  P, n, cs.beta, cs.Ahat.p);
+    } else if (cs.na == 1) {
+        if ((rc = cs.Ahat.alloc((size_t)m_pad * n_pad * 2))) return rc;
+        k_scale_round<1><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
+                                                  P, n, cs.beta, cs.Ahat.p);
+    } else {
+        if ((rc = cs.A32.alloc((size_t)m_pad * n_pad * 4))) return rc;
+        k_scale_round<0><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
+                                                  P, n, cs.beta, cs.A32.p);
+    }
+    LGK_LAUNCH_CHECK();
+
+    // ---- S = A A^T + I (FP64, from the rounded A), Cholesky, inverse
+    DevBuf S, Y;
+    if ((rc = S.alloc((size_t)m_pad * m_pad * 8))) return rc;
+    if ((rc = dgemm_lower_nt(st, m_pad, n_pad, 1.0, A64.as<double>(), n_pad, 0.0, S.as<double>(), m_pad)))
+        return rc;
+    k_add_identity<<<(m_pad + 255) / 256, 256, 0, st>>>(S.as<double>(), m_pad, m_pad);
+    LGK_LAUNCH_CHECK();
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    A64.alloc(0);
+
+    double* Sd = S.as<double>();
+    int* err = cs.ctrl_setup.as<int>();
+    for (int k0 = 0; k0 < m_pad; k0 += NB) {
+        k_potrf_diag<<<1, 256, 0, st>>>(Sd, m_pad, k0, err);
+        LGK_LAUNCH_CHECK();
+        int rows = m_pad - k0 - NB;
+        if (rows > 0) {
+            k_trsm_panel<<<(rows + 127) / 128, 128, 0, st>>>(Sd, m_pad, k0, m_pad);
+            LGK_LAUNCH_CHECK();
+            double* panel = Sd + (size_t)(k0 + NB) * m_pad + k0;
+            double* trail = Sd + (size_t)(k0 + NB) * m_pad + k0 + NB;
+            if ((rc = dgemm_lower_nt(st, rows, NB, -1.0, panel, m_pad, 1.0, trail, m_pad))) return rc;
+        }
+    }
+    k_zero_upper<<<148 * 8, 256, 0, st>>>(Sd, m_pad, m_pad);
+    LGK_LAUNCH_CHECK();
+    int h_err = 0;
+    LGK_CUDA_TRY(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h_err == DERR_NOT_PD) {
+        set_error("S = A A^T + I is not positive definite in FP64 (Cholesky pivot <= 0)");
+        return LGK_ENOTPD;
+    }
+    // Y = L^{-1} by blocked forward substitution on the identity
+    if ((rc = Y.alloc((size_t)m_pad * m_pad * 8))) return rc;
+    double* Yd = Y.as<double>();
+    k_set_identity<<<148 * 8, 256, 0, st>>>(Yd, m_pad, m_pad);
+    LGK_LAUNCH_CHECK();
+    for (int k0 = 0; k0 < m_pad; k0 += NB) {
+        int ncols = k0 + NB;
+        k_trsm_rows<<<(ncols + 127) / 128, 128, 0, st>>>(Sd, m_pad, Yd, m_pad, k0, ncols);
+        LGK_LAUNCH_CHECK();
+        int rows = m_pad - k0 - NB;
+        if (rows > 0) {
+            if ((rc = dgemm(st, false, false, rows, ncols, NB, -1.0, Sd + (size_t)(k0 + NB) * m_pad + k0,
+                            m_pad, Yd + (size_t)k0 * m_pad, m_pad, 1.0, Yd + (size_t)(k0 + NB) * m_pad,
+                            m_pad)))
+                return rc;
+        }
+    }
+    // S^{-1} = L^{-T} L^{-1} = Y^T Y (reuse the S buffer)
+    if ((rc = dgemm(st, true, false, m_pad, m_pad, m_pad, 1.0, Yd, m_pad, Yd, m_pad, 0.0, Sd, m_pad)))
+        return rc;
+    size_t mm = (size_t)m_pad * m_pad;
+    if (bf16) {
+        if ((rc = cs.G3.alloc(mm * 3 * 2))) return rc;
+        k_inverse_out<<<148 * 8, 256, 0, st>>>(Sd, mm, nullptr, cs.G3.as<__nv_bfloat16>());
+    } else {
+        if ((rc = cs.G32.alloc(mm * 4))) return rc;
+        k_inverse_out<<<148 * 8, 256, 0, st>>>(Sd, mm, cs.G32.as<float>(), nullptr);
+    }
+    LGK_LAUNCH_CHECK();
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    return LGK_OK;
+}
+
+}  // namespace lgk

@@ -1,0 +1,239 @@
+"""Python binding of liblgk.so (ctypes).  Argument marshalling only: every
+step of the planning path runs in the library's CUDA kernels.
+
+The names mirror the C ABI of include/lgk.h without the `lgk_` prefix:
+create_case, solve_weightings, fetch_times, fetch_doses, fetch_stats,
+fetch_state.  The library must have been built (paper_2509_08602_b300.build);
+importing this module without it raises ImportError rather than falling back
+to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblgk.so")
+
+PREC_FP32 = 0
+PREC_BF16 = 1
+PREC_BF16X3 = 2
+STATUS = {0: "LGK_OK", 1: "LGK_EINVAL", 2: "LGK_ENOMEM", 3: "LGK_EBUDGET", 4: "LGK_ENOTPD",
+          5: "LGK_ECUDA", 6: "LGK_ETIMEOUT"}
+
+
+class LgkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CaseDesc(C.Structure):
+    _fields_ = [("n_iso", C.c_int), ("n_pts", C.c_int), ("n_targets", C.c_int), ("n_oars", C.c_int),
+                ("phi", C.POINTER(C.c_double)), ("kind", C.POINTER(C.c_uint8)),
+                ("struct_id", C.POINTER(C.c_uint16)), ("d_presc", C.POINTER(C.c_double)),
+                ("q_area", C.POINTER(C.c_double)), ("q_vol", C.POINTER(C.c_double)),
+                ("d_oar", C.POINTER(C.c_double)), ("d_ld1", C.c_double), ("d_ld2", C.c_double),
+                ("phi_cal", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("precision", C.c_int), ("normalize_rows", C.c_int), ("scale_bot", C.c_int),
+                ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
+                ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
+                ("profile", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_2509_08602_b300.build`")
+    lib = C.CDLL(_LIB_PATH)
+    P = C.POINTER
+    lib.lgk_default_params.argtypes = [P(Params)]
+    lib.lgk_create_case.argtypes = [P(CaseDesc), P(Params), P(C.c_void_p)]
+    lib.lgk_case_info.argtypes = [C.c_void_p, P(C.c_int), P(C.c_int), P(C.c_double), P(C.c_size_t)]
+    lib.lgk_solve_weightings.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
+                                         C.c_double, C.c_double, C.c_double, C.c_int, P(C.c_void_p)]
+    lib.lgk_fetch_times.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
+    lib.lgk_fetch_doses.argtypes = [C.c_void_p, P(C.c_double), C.c_int, P(C.c_double)]
+    lib.lgk_fetch_stats.argtypes = [C.c_void_p, P(C.c_int), P(C.c_double), P(C.c_double),
+                                    P(C.c_double), P(C.c_uint8)]
+    lib.lgk_fetch_state.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double)]
+    lib.lgk_solve_weightings_warm.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
+                                              C.c_double, C.c_double, C.c_double, C.c_int,
+                                              P(C.c_double), P(C.c_double), P(C.c_void_p)]
+    lib.lgk_fetch_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_longlong)]
+    lib.lgk_free_result.argtypes = [C.c_void_p]
+    lib.lgk_destroy_case.argtypes = [C.c_void_p]
+    lib.lgk_last_error.restype = C.c_char_p
+    lib.lgk_launch_count.restype = C.c_longlong
+    for f in ("lgk_default_params", "lgk_create_case", "lgk_case_info", "lgk_solve_weightings",
+              "lgk_fetch_times", "lgk_fetch_doses", "lgk_fetch_stats", "lgk_fetch_state",
+              "lgk_solve_weightings_warm", "lgk_fetch_profile"):
+        getattr(lib, f).restype = C.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LgkError(rc, _lib.lgk_last_error().decode(errors="replace"))
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(_lib.lgk_default_params(C.byref(p)))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Case:
+    """Device-resident planning case (lgk_case)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+        m, n, beta, nbytes = C.c_int(), C.c_int(), C.c_double(), C.c_size_t()
+        _check(_lib.lgk_case_info(handle, C.byref(m), C.byref(n), C.byref(beta), C.byref(nbytes)))
+        self.m, self.n, self.beta, self.device_bytes = m.value, n.value, beta.value, nbytes.value
+
+    def close(self):
+        if self._h:
+            _lib.lgk_destroy_case(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Result:
+    """Solved batch of weightings (lgk_result)."""
+
+    def __init__(self, handle, K, case):
+        self._h = handle
+        self.K = K
+        self.case = case
+
+    def close(self):
+        if self._h:
+            _lib.lgk_free_result(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def create_case(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal,
+                d_oar=None, params: Params | None = None) -> Case:
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    struct_id = np.ascontiguousarray(struct_id, dtype=np.uint16)
+    d_presc = np.ascontiguousarray(np.atleast_1d(d_presc), dtype=np.float64)
+    q_area = np.ascontiguousarray(np.atleast_1d(q_area), dtype=np.float64)
+    q_vol = np.ascontiguousarray(np.atleast_1d(q_vol), dtype=np.float64)
+    d_oar = None if d_oar is None or len(d_oar) == 0 else np.ascontiguousarray(d_oar, dtype=np.float64)
+    d = CaseDesc(n_iso=int(n_iso), n_pts=int(phi.shape[0]), n_targets=int(d_presc.shape[0]),
+                 n_oars=0 if d_oar is None else int(d_oar.shape[0]),
+                 phi=_ptr(phi, C.c_double), kind=_ptr(kind, C.c_uint8),
+                 struct_id=_ptr(struct_id, C.c_uint16), d_presc=_ptr(d_presc, C.c_double),
+                 q_area=_ptr(q_area, C.c_double), q_vol=_ptr(q_vol, C.c_double),
+                 d_oar=_ptr(d_oar, C.c_double), d_ld1=float(d_ld1), d_ld2=float(d_ld2),
+                 phi_cal=float(phi_cal))
+    if phi.shape[1] != 24 * int(n_iso) or kind.shape[0] != phi.shape[0] or struct_id.shape[0] != phi.shape[0]:
+        raise LgkError(1, "phi must be n_pts x 24 n_iso; kind and struct_id of length n_pts")
+    h = C.c_void_p()
+    _check(_lib.lgk_create_case(C.byref(d), C.byref(params) if params is not None else None,
+                                C.byref(h)))
+    return Case(h, None)
+
+
+def solve_weightings(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 0.0,
+                     tol: float = 1e-4, max_iter: int = 10000) -> Result:
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    if W.shape[1] != 4:
+        raise LgkError(1, "W must be K x 4")
+    K = W.shape[0]
+    r = None if rho is None else np.ascontiguousarray(np.broadcast_to(rho, (K,)), dtype=np.float64)
+    h = C.c_void_p()
+    _check(_lib.lgk_solve_weightings(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double),
+                                     float(w0_bot), float(rho0), float(tol), int(max_iter),
+                                     C.byref(h)))
+    return Result(h, K, case)
+
+
+def solve_weightings_warm(case: Case, W, rho=None, *, q1_init=None, q2_init=None,
+                          w0_bot: float = 0.0, rho0: float = 0.0, tol: float = 1e-4,
+                          max_iter: int = 10000) -> Result:
+    """Resume from a q-form state (K x n, K x m) such as fetch_state returns."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K = W.shape[0]
+    r = None if rho is None else np.ascontiguousarray(np.broadcast_to(rho, (K,)), dtype=np.float64)
+    q1 = None if q1_init is None else np.ascontiguousarray(q1_init, dtype=np.float64)
+    q2 = None if q2_init is None else np.ascontiguousarray(q2_init, dtype=np.float64)
+    if q1 is not None and q1.shape != (K, case.n) or q2 is not None and q2.shape != (K, case.m):
+        raise LgkError(1, "q1_init must be K x n and q2_init K x m")
+    h = C.c_void_p()
+    _check(_lib.lgk_solve_weightings_warm(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double),
+                                          float(w0_bot), float(rho0), float(tol), int(max_iter),
+                                          _ptr(q1, C.c_double), _ptr(q2, C.c_double), C.byref(h)))
+    return Result(h, K, case)
+
+
+def fetch_times(res: Result):
+    """(t (K x 24N), tau (K x N)) as FP64."""
+    n_iso = (res.case.m) // 25
+    t = np.empty((res.K, 24 * n_iso))
+    tau = np.empty((res.K, n_iso))
+    _check(_lib.lgk_fetch_times(res._h, _ptr(t, C.c_double), _ptr(tau, C.c_double)))
+    return t, tau
+
+
+def fetch_doses(res: Result, phi_eval) -> np.ndarray:
+    phi_eval = np.ascontiguousarray(phi_eval, dtype=np.float64)
+    dose = np.empty((res.K, phi_eval.shape[0]))
+    _check(_lib.lgk_fetch_doses(res._h, _ptr(phi_eval, C.c_double), int(phi_eval.shape[0]),
+                                _ptr(dose, C.c_double)))
+    return dose
+
+
+def fetch_stats(res: Result) -> dict:
+    K = res.K
+    it = np.empty(K, np.int32)
+    obj, rp, rd = np.empty(K), np.empty(K), np.empty(K)
+    conv = np.empty(K, np.uint8)
+    _check(_lib.lgk_fetch_stats(res._h, _ptr(it, C.c_int), _ptr(obj, C.c_double), _ptr(rp, C.c_double),
+                                _ptr(rd, C.c_double), _ptr(conv, C.c_uint8)))
+    return dict(iters=it, obj=obj, rel_pri=rp, rel_dual=rd, converged=conv.astype(bool))
+
+
+def fetch_state(res: Result):
+    """(q1 (K x n), q2 (K x m)): the q-form ADMM state of the scaled problem,
+    q = z + y, FP64."""
+    q1 = np.empty((res.K, res.case.n))
+    q2 = np.empty((res.K, res.case.m))
+    _check(_lib.lgk_fetch_state(res._h, _ptr(q1, C.c_double), _ptr(q2, C.c_double)))
+    return q1, q2
+
+
+KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "finalize")
+
+
+def fetch_profile(res: Result) -> dict:
+    """{kernel: (total ms, timed launches)} of a solve made with profile=1."""
+    ms = np.zeros(len(KERNELS))
+    n = np.zeros(len(KERNELS), np.int64)
+    _check(_lib.lgk_fetch_profile(res._h, _ptr(ms, C.c_double), _ptr(n, C.c_longlong)))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library on this thread since the last call."""
+    return int(_lib.lgk_launch_count())

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Precision forms: 0 = FP32 (cuBLAS comparison form), 1 = BF16 (A rounded to
+one BF16 term), 2 = BF16X3 (A as two BF16 terms; the product form).
+
+Tolerances (derived in DESIGN.md, "Tolerances"):
+  * one iteration from a common state, element by element on the same LP (the
+    matrix each form actually iterates on: FP32-rounded, BF16-rounded, or the
+    two-term BF16 sum): max |gpu - oracle| <= ||A||_2^2 u max |q| with
+    u = 2^-17 for the BF16 forms (iterates split into two BF16 terms) and
+    u = 2^-24 sqrt(n) for FP32 (FP32 sums of n terms); S^{-1} has norm <= 1
+    since S = I + A A^T;
+  * converged plans (tol 1e-4) of the FP32 and BF16X3 forms against the FP64
+    oracle on the exact matrix: |obj - obj*| / max(1, |obj*|) <= 1e-3 against
+    the simplex optimum, relative primal/dual residual <= 1e-4, coverage,
+    selectivity, gradient index and beam-on time within 0.5 % of the oracle
+    ADMM plan.  The one-term BF16 form solves the LP of the rounded matrix and
+    is held to the same bars against the oracle run on that matrix.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm as AD
+from oracle import lp as L
+from oracle import metrics as M
+from oracle import simplex as SX
+from synth import cases as SC
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lgk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_08602_b300 import build
+    build.build()
+    from paper_2509_08602_b300 import lgk as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    case = SC.workload_case(0)
+    lp = L.precondition(L.assemble_case(case))
+    W = SC.slider_weights(3)
+    b, l, u = L.bounds(lp, W)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    opt = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(W.shape[0])])
+    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=TOL)
+    pts, label, _ = SC.eval_grid(case, spacing=1.0, margin=12.0)
+    phi_eval = SC.dose_rate(pts, case.iso)
+    t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
+    met_ref = M.plan_metrics(M.dose(phi_eval, t_ref), label, case.d_presc, t_ref, case.n_iso)
+    return dict(case=case, lp=lp, W=W, b=b, l=l, u=u, rho=rho, opt=opt, ref=ref,
+                phi_eval=phi_eval, label=label, met_ref=met_ref)
+
+
+def make(lgk, case, prec, **kw):
+    return lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                           case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                           params=lgk.default_params(precision=prec, **kw))
+
+
+PRECS = [0, 1, 2]
+PREC_IDS = ["fp32", "bf16", "bf16x3"]
+
+
+def lp_matrix(lp, lgk, prec):
+    """The matrix the device iterates on."""
+    if prec == lgk.PREC_FP32:
+        return lp.A.astype(np.float32).astype(np.float64)
+    hi = L.bf16_round(lp.A)
+    if prec == lgk.PREC_BF16:
+        return hi
+    return hi + L.bf16_round(lp.A - hi)
+
+
+def unit_roundoff(lgk, prec, n):
+    return 2.0 ** -24 * np.sqrt(n) if prec == lgk.PREC_FP32 else 2.0 ** -17
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_one_iteration_from_common_state(lgk, cfg0, prec):
+    """Device and oracle start from the oracle's state after k iterations and
+    take one iteration of Eq. admm; the states agree element by element."""
+    c = cfg0
+    cs = make(lgk, c["case"], prec)
+    A = lp_matrix(c["lp"], lgk, prec)
+    tol = np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, prec, A.shape[1])
+    for k in (0, 30, 300):
+        ok = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=k)
+        q1, q2 = (ok.z1 + ok.y1).T, (ok.z2 + ok.y2).T
+        res = lgk.solve_weightings_warm(cs, c["W"], c["rho"], q1_init=q1, q2_init=q2, tol=0.0,
+                                        max_iter=1)
+        g1, g2 = lgk.fetch_state(res)
+        o = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=1,
+                    state=(ok.z1, ok.z2, ok.y1, ok.y2))
+        r1, r2 = o.z1 + o.y1, o.z2 + o.y2
+        assert np.abs(g1.T - r1).max() <= tol * np.abs(r1).max(), k
+        assert np.abs(g2.T - r2).max() <= tol * np.abs(r2).max(), k
+        z1 = np.clip(g1.T, c["l"], c["u"])
+        assert np.abs(z1 - o.z1).max() <= tol * np.abs(r1).max(), k
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_short_trajectory_from_zero(lgk, cfg0, prec):
+    """Five iterations from z = y = 0 (cold start); rounding differences grow
+    along the trajectory, so the bound is five one-step bounds."""
+    c = cfg0
+    cs = make(lgk, c["case"], prec)
+    A = lp_matrix(c["lp"], lgk, prec)
+    tol = 5 * np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, prec, A.shape[1])
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=5)
+    st = lgk.fetch_stats(res)
+    assert np.all(st["iters"] == 5) and not st["converged"].any()
+    g1, g2 = lgk.fetch_state(res)
+    o = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=5)
+    r1, r2 = o.z1 + o.y1, o.z2 + o.y2
+    assert np.abs(g1.T - r1).max() <= tol * np.abs(r1).max()
+    assert np.abs(g2.T - r2).max() <= tol * np.abs(r2).max()
+    # projections are exact on the device: y2 = q2 - min(q2, b) >= 0
+    assert np.all(g2.T - np.minimum(g2.T, c["b"]) >= 0)
+
+
+def test_warm_start_resumes_the_iteration(lgk, cfg0):
+    """Checkpoint / resume: 30 iterations, fetch the state, 20 more from it
+    equals 50 straight (same arithmetic, bit for bit)."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    a = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=30)
+    q1, q2 = lgk.fetch_state(a)
+    b = lgk.solve_weightings_warm(cs, c["W"], c["rho"], q1_init=q1, q2_init=q2, tol=0.0, max_iter=20)
+    full = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=50)
+    np.testing.assert_array_equal(lgk.fetch_state(b)[0], lgk.fetch_state(full)[0])
+    np.testing.assert_array_equal(lgk.fetch_state(b)[1], lgk.fetch_state(full)[1])
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PREC_IDS)
+def test_converged_parity_cfg0(lgk, cfg0, prec):
+    c = cfg0
+    case, lp = c["case"], c["lp"]
+    if prec == lgk.PREC_BF16:        # its own LP: the oracle on the rounded matrix
+        A = lp_matrix(lp, lgk, prec)
+        opt = np.array([SX.simplex(A, c["b"][:, j], lp.c, c["u"][:, j]).obj for j in range(9)])
+        ref = AD.admm(A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=TOL)
+        t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
+        met_ref = M.plan_metrics(M.dose(c["phi_eval"], t_ref), c["label"], case.d_presc, t_ref,
+                                 case.n_iso)
+    else:
+        opt, met_ref = c["opt"], c["met_ref"]
+    cs = make(lgk, case, prec)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
+    assert gap.max() <= 1e-3
+    assert st["rel_pri"].max() <= TOL and st["rel_dual"].max() <= TOL
+    t, tau = lgk.fetch_times(res)
+    assert np.all(t >= 0) and np.all(tau >= 0)
+    dose = lgk.fetch_doses(res, c["phi_eval"])
+    # device dose = phi_eval t exactly up to FP64 rounding
+    np.testing.assert_allclose(dose, (c["phi_eval"] @ t.T).T, rtol=1e-12, atol=1e-12)
+    met = M.plan_metrics(dose.T, c["label"], case.d_presc, t.T, case.n_iso)
+    for key in ("coverage", "selectivity", "gi", "bot"):
+        rel = np.abs(met[key] - met_ref[key]) / np.abs(met_ref[key])
+        assert rel.max() <= 5e-3, (key, rel)
+
+
+def test_batch_independence(lgk, cfg0):
+    """A weighting's iterates do not depend on the batch it is solved in."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    full = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=100)
+    z_full, y_full = lgk.fetch_state(full)
+    one = lgk.solve_weightings(cs, c["W"][4:5], c["rho"][4:5], tol=0.0, max_iter=100)
+    z_one, y_one = lgk.fetch_state(one)
+    np.testing.assert_array_equal(z_one[0], z_full[4])
+    np.testing.assert_array_equal(y_one[0], y_full[4])
+
+
+def test_ragged_batch_and_degenerate_columns(lgk, cfg0):
+    """K = 17 (not a multiple of 16) with a zero target weight (empty plan)
+    and a zero low-dose weight; every column reaches its simplex optimum.
+    Solved to 5e-5 so the objective bar has headroom over the stop test."""
+    c = cfg0
+    lp = c["lp"]
+    rng = np.random.default_rng(7)
+    W = np.column_stack([np.ones(17), np.ones(17), rng.uniform(0, 1, 17),
+                         SC.W0_BOT * 10 ** rng.uniform(0, 3, 17)])
+    W[3, 0] = 0.0
+    W[3, 1] = 0.0
+    W[3, 2] = 0.0
+    W[5, 2] = 0.0
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    cs = make(lgk, c["case"], 2)
+    res = lgk.solve_weightings(cs, W, rho, tol=5e-5, max_iter=40000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    b, _, u = L.bounds(lp, W)
+    for j in range(17):
+        opt = SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj
+        assert abs(st["obj"][j] - opt) <= 1e-3 * max(1.0, abs(opt))
+    t, _ = lgk.fetch_times(res)
+    assert np.abs(t[3]).max() <= 1e-6 * np.abs(t).max()
+
+
+def test_rho_rule_inside_library(lgk, cfg0):
+    """rho = NULL applies Eq. rho_rule in the library: same iterates as
+    passing the rule's values explicitly."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    a = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=20)
+    b = lgk.solve_weightings(cs, c["W"], None, w0_bot=SC.W0_BOT, rho0=L.RHO0, tol=0.0, max_iter=20)
+    za, _ = lgk.fetch_state(a)
+    zb, _ = lgk.fetch_state(b)
+    np.testing.assert_allclose(za, zb, rtol=1e-6, atol=1e-12)
+
+
+def test_budget_and_timeout_errors(lgk, cfg0):
+    c = cfg0
+    with pytest.raises(lgk.LgkError) as e:
+        make(lgk, c["case"], 2, hbm_budget=1 << 20)
+    assert e.value.code == 3            # LGK_EBUDGET
+    cs = make(lgk, c["case"], 2, timeout_ms=1)
+    with pytest.raises(lgk.LgkError) as e:
+        lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=200000)
+    assert e.value.code == 6            # LGK_ETIMEOUT, host wait bounded
+    # the case stays usable afterwards
+    cs2 = make(lgk, c["case"], 2)
+    res = lgk.solve_weightings(cs2, c["W"], c["rho"], tol=0.0, max_iter=5)
+    assert np.all(lgk.fetch_stats(res)["iters"] == 5)
