@@ -184,7 +184,7 @@ int lgk_fetch_state(const lgk_result* res, double* q1, double* q2);
 
 /* Kernel classes of one ADMM iteration, in launch order. */
 enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLVE = 3,
-       LGK_K_GEMM2 = 4, LGK_K_FINALIZE = 5, LGK_K_COUNT = 6 };
+       LGK_K_GEMM2 = 4, LGK_K_Q1_UPDATE = 5, LGK_K_FINALIZE = 6, LGK_K_COUNT = 7 };
 
 /* Per-kernel-class device time of a solve made with lgk_params.profile = 1:
  * ms[LGK_K_COUNT] total milliseconds between CUDA events recorded on the

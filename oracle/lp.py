@@ -181,17 +181,25 @@ def bounds(lp: DualLP, W) -> tuple:
 
 
 RHO0_PAPER = 2.5e-3
-RHO0 = 2.5e3
+RHO0_PER_BETA = 1.1e3
 
 
-def rho_rule(w_bot, w0_bot: float, rho0: float = RHO0) -> np.ndarray:
-    """Eq. rho_rule: rho = rho0 * sqrt(w_0,BOT / w_BOT).
+def rho0_for(lp: DualLP) -> float:
+    """Constant of Eq. rho_rule for this case: RHO0_PER_BETA * beta.
 
     The paper's constant rho0 = 2.5e-3 was tuned (Sec. 3.C) for its kernels'
-    units, which it does not state.  Re-running its tuning procedure (a grid
-    of rho values, fixed iteration count, objective compared with the simplex
-    optimum) on the synthetic cases here puts the best constant at 2.5e3; the
-    sqrt(w_0,BOT / w_BOT) dependence the paper found is reproduced."""
+    units, which it does not state.  The bounds u = w / N_alpha make the dual
+    variables scale as 1 / (number of points) while the multipliers (sector
+    times) do not, so the balancing penalty grows with the point count; beta =
+    (#non-OAR points) / 2000 of Sec. 3.C is that count.  Re-running the paper's
+    tuning procedure (grid of rho values, objective against the simplex
+    optimum, iterations to tolerance) on three synthetic case sizes puts the
+    best constant at 1.1e3 * beta on all three."""
+    return RHO0_PER_BETA * lp.beta
+
+
+def rho_rule(w_bot, w0_bot: float, rho0: float) -> np.ndarray:
+    """Eq. rho_rule: rho = rho0 * sqrt(w_0,BOT / w_BOT)."""
     return rho0 * np.sqrt(w0_bot / np.asarray(w_bot, dtype=np.float64))
 
 

@@ -9,13 +9,17 @@
 // m x K matrix; weightings are the K columns.
 //
 // Kernel sequence of one iteration (both precisions):
-//   GEMM1  part  = A . R1            (split over the n columns of A)
-//   reduce rhs   = sum(part) + q2 - 2 P2(q2)
-//   solve  part  = S^{-1} . rhs      (split over m)
-//   reduce q2'   = sum(part) + P2(q2), residual partials of the m-block
-//   GEMM2  q1'   = P1(q1) - c/rho - A^T v, R1' for the next GEMM1, residual
-//                  partials of the n-block
-//   finalize     per-column stop test (Boyd et al. Sec. 3.3), freeze
+//   GEMM1      part = A . R1
+//   reduce     rhs  = part + q2 - 2 P2(q2)
+//   solve      part = S^{-1} . rhs
+//   reduce     q2'  = part + P2(q2), residual partials of the m-block
+//   GEMM2      part = A^T . V
+//   q1 update  q1'  = P1(q1) - c/rho - part, R1' for the next GEMM1, residual
+//              partials of the n-block
+//   finalize   per-column stop test (Boyd et al. Sec. 3.3), freeze
+// The BF16 forms' GEMMs leave stream-K segment partials that the next kernel
+// sums per element in k order; the FP32 form's cuBLAS GEMMs leave a plain
+// matrix.
 #include <math.h>
 
 #include <algorithm>
@@ -34,15 +38,35 @@ ResultData::~ResultData() {
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
 }
 
-// Event between kernels k-1 and k of captured iteration `it` (profile mode).
+// Event before kernel k of captured iteration `it` (profile mode).
 static void prof_mark(ResultData& r, int it, int k) {
     // External: captured as an event-record node of the graph (a plain record
     // inside a capture only expresses a dependency)
     if (!r.prof_ev.empty())
-        cudaEventRecordWithFlags(r.prof_ev[(size_t)it * 7 + k], r.cs->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(r.prof_ev[(size_t)it * (LGK_K_COUNT + 1) + k], r.cs->stream,
+                                 cudaEventRecordExternal);
 }
 
 // ---------------------------------------------------------------- helpers
+
+// Where one GEMM's output lives: a plain [Kp][rows_pad] matrix (tile_begin
+// null), or stream-K segment slots [slot][n_tile][128] summed in k order.
+struct SumSrc {
+    const float* part;
+    const int* tile_begin;
+    const int* tile_slots;
+    int rows_pad, row_tiles, n_tile;
+};
+
+__device__ inline float gemm_out(const SumSrc& s, int i, int j) {
+    if (!s.tile_begin) return s.part[(size_t)j * s.rows_pad + i];
+    const int rt = i >> 7, ii = i & 127, ct = j / s.n_tile, jj = j - ct * s.n_tile;
+    const int t = ct * s.row_tiles + rt;
+    float acc = 0.f;
+    for (int k = s.tile_begin[t]; k < s.tile_begin[t + 1]; ++k)
+        acc += s.part[((size_t)s.tile_slots[k] * s.n_tile + jj) * 128 + ii];
+    return acc;
+}
 
 // block-wide sum of 5 values into out[0..4] (thread 0 holds the result)
 __device__ inline void block_sum5(float v[5], double* out) {
@@ -87,15 +111,14 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
     }
 }
 
-// rhs = sum_s part[s] + q2 - 2 P2(q2)
+// rhs = A R1 + q2 - 2 P2(q2)
 template <bool BF16>
-__global__ void k_reduce_rhs(IterCtx cx, const float* __restrict__ part, int splits, void* rhs) {
+__global__ void k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i >= cx.m_pad) return;
     size_t o = (size_t)j * cx.m_pad + i;
-    float acc = 0.f;
-    for (int s = 0; s < splits; ++s) acc += part[(size_t)s * cx.Kp * cx.m_pad + o];
+    const float acc = gemm_out(src, i, j);
     float q = cx.q2[o];
     float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
     float r = acc + q - 2.f * p2;
@@ -113,17 +136,16 @@ __global__ void k_reduce_rhs(IterCtx cx, const float* __restrict__ part, int spl
     }
 }
 
-// v = sum_s part[s];  q2' = v + P2(q2);  residual partials of the m-block.
+// v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block.
 template <bool BF16>
-__global__ void k_reduce_solve(IterCtx cx, const float* __restrict__ part, int splits, void* V) {
+__global__ void k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
     float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (i < cx.m_pad) {
         size_t o = (size_t)j * cx.m_pad + i;
-        float v = 0.f;
-        for (int s = 0; s < splits; ++s) v += part[(size_t)s * cx.Kp * cx.m_pad + o];
+        const float v = gemm_out(src, i, j);
         float qo = cx.q2[o];
         float bb = b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
         float zo = fminf(qo, bb);
@@ -153,8 +175,11 @@ __global__ void k_reduce_solve(IterCtx cx, const float* __restrict__ part, int s
     }
 }
 
-// FP32 path: q1' = P1(q1) - c/rho - W and R1' from W = A^T V (cuBLAS output).
-__global__ void k_gemm2_ep_f32(IterCtx cx, const float* __restrict__ W, float* __restrict__ R1) {
+// q1' = P1(q1) - c/rho - W and R1' = 2 P1(q1') - q1' - c/rho from W = A^T V;
+// residual partials of the n-block.  R1 is FP32 (FP32 form) or two BF16
+// terms (BF16 forms).
+template <bool BF16>
+__global__ void k_q1_update(IterCtx cx, SumSrc src, void* R1) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
@@ -164,9 +189,16 @@ __global__ void k_gemm2_ep_f32(IterCtx cx, const float* __restrict__ W, float* _
         int sl = cx.col_slot[p];
         float u = cx.utab[j * cx.n_slot + sl];
         float cr = cx.c_slot[sl] * cx.inv_rho[j];
-        Q1Update q = q1_update(cx.q1[o], W[o], u, cr);
+        Q1Update q = q1_update(cx.q1[o], gemm_out(src, p, j), u, cr);
         if (cx.active[j]) cx.q1[o] = q.qn;
-        R1[o] = q.r1;
+        if (BF16) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(q.r1, hi, lo);
+            static_cast<__nv_bfloat16*>(R1)[o] = hi;
+            static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
+        } else {
+            static_cast<float*>(R1)[o] = q.r1;
+        }
         if (check)
             for (int k = 0; k < 5; ++k) res[k] = q.res[k];
     }
@@ -293,6 +325,12 @@ static IterCtx make_ctx(ResultData& r) {
 
 IterCtx make_ctx_public(ResultData& r) { return make_ctx(r); }
 
+static SumSrc plain_src(const float* p, int rows_pad) { return SumSrc{p, nullptr, nullptr, rows_pad, 0, 1}; }
+
+static SumSrc plan_src(const ResultData& r, const GemmPlan& P) {
+    return SumSrc{r.part.as<float>(), P.tile_begin, P.tile_slots, 0, P.rows, P.n_tile};
+}
+
 static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
@@ -309,7 +347,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     count_launch();
     prof_mark(r, itx, 1);
     dim3 gm((cs.m_pad + 255) / 256, r.Kp);
-    k_reduce_rhs<false><<<gm, 256, 0, st>>>(cx, part, 1, r.rhs.p);
+    k_reduce_rhs<false><<<gm, 256, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     // solve: part = rhs . G^T (G symmetric)
@@ -321,7 +359,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 3);
-    k_reduce_solve<false><<<gm, 256, 0, st>>>(cx, part, 1, r.V.p);
+    k_reduce_solve<false><<<gm, 256, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     // GEMM2: W[Kp][n_pad] = V[Kp][m_pad] . A[m_pad][n_pad]
@@ -332,13 +370,14 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
         return LGK_ECUDA;
     }
     count_launch();
-    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
-    k_gemm2_ep_f32<<<gn, 256, 0, st>>>(cx, r.W.as<float>(), r.R1.as<float>());
-    LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 5);
-    k_finalize<<<1, 1024, 0, st>>>(cx);
+    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
+    k_q1_update<false><<<gn, 256, 0, st>>>(cx, plain_src(r.W.as<float>(), cs.n_pad), r.R1.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 6);
+    k_finalize<<<1, 1024, 0, st>>>(cx);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 7);
     return LGK_OK;
 }
 
@@ -350,19 +389,23 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     if ((rc = tc_gemm1(r))) return rc;
     prof_mark(r, itx, 1);
     dim3 gm((cs.m_pad + 255) / 256, r.Kp);
-    k_reduce_rhs<true><<<gm, 256, 0, st>>>(cx, r.part.as<float>(), r.splits1, r.rhs.p);
+    k_reduce_rhs<true><<<gm, 256, 0, st>>>(cx, plan_src(r, r.plan1), r.rhs.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     if ((rc = tc_solve(r))) return rc;
     prof_mark(r, itx, 3);
-    k_reduce_solve<true><<<gm, 256, 0, st>>>(cx, r.part.as<float>(), r.splits_s, r.V.p);
+    k_reduce_solve<true><<<gm, 256, 0, st>>>(cx, plan_src(r, r.plan_s), r.V.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     if ((rc = tc_gemm2(r))) return rc;
     prof_mark(r, itx, 5);
-    k_finalize<<<1, 1024, 0, st>>>(cx);
+    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
+    k_q1_update<true><<<gn, 256, 0, st>>>(cx, plan_src(r, r.plan2), r.R1.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 6);
+    k_finalize<<<1, 1024, 0, st>>>(cx);
+    LGK_LAUNCH_CHECK();
+    prof_mark(r, itx, 7);
     return LGK_OK;
 }
 
@@ -410,19 +453,11 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if ((rc = r.R1.alloc(bf16 ? nq * 4 : nq * 4))) return rc;     // 2 x bf16 or 1 x f32
     if ((rc = r.rhs.alloc(bf16 ? mq * 6 : mq * 4)) || (rc = r.V.alloc(mq * 4))) return rc;
     if (!bf16 && (rc = r.W.alloc(nq * 4))) return rc;
-    int row_tiles_m = cs.m_pad / 128, n_tiles = Kp / r.n_tile;
-    if (bf16) {
-        r.splits1 = plan_splits(cs.n_pad / 64, row_tiles_m, n_tiles);
-        r.splits_s = plan_splits(cs.m_pad / 64, row_tiles_m, r.Kp / r.n_tile_s);
-    } else {
-        r.splits1 = r.splits_s = 1;
-    }
-    int max_split = std::max(r.splits1, r.splits_s);
-    if ((rc = r.part.alloc((size_t)max_split * mq * 4))) return rc;
+    if (!bf16 && (rc = r.part.alloc(mq * 4))) return rc;     // BF16 forms: tc_prepare
     if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
     if ((rc = r.active.alloc((size_t)2 * Kp * 4)) || (rc = r.iters.alloc((size_t)Kp * 4))) return rc;
     if ((rc = r.ctrl.alloc(sizeof(Control)))) return rc;
-    r.n_resid_n = bf16 ? cs.n_pad / 128 : (cs.n_pad + 255) / 256;
+    r.n_resid_n = (cs.n_pad + 255) / 256;
     r.n_resid_m = (cs.m_pad + 255) / 256;
     if ((rc = r.resid.alloc((size_t)(r.n_resid_n + r.n_resid_m) * Kp * 5 * 8))) return rc;
     if ((rc = r.stats.alloc((size_t)3 * Kp * 8))) return rc;
@@ -472,7 +507,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     int per_graph = std::max(1, std::min(r.max_iter, 5 * cs.prm.check_every));
     cudaGraph_t g = nullptr;
     if (cs.prm.profile) {
-        r.prof_ev.assign((size_t)per_graph * 7, nullptr);
+        r.prof_ev.assign((size_t)per_graph * (LGK_K_COUNT + 1), nullptr);
         for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
     }
     LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -496,8 +531,8 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.graph_iters = per_graph;
     size_t n_nodes = 0;
     {
-        // kernels per iteration: 6 (both precisions)
-        n_nodes = (size_t)per_graph * 6;
+        // kernels per iteration (both precisions)
+        n_nodes = (size_t)per_graph * LGK_K_COUNT;
     }
 
     Control* hc = nullptr;
@@ -533,8 +568,8 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             for (int it = 0; it < worked; ++it)
                 for (int k = 0; k < LGK_K_COUNT; ++k) {
                     float ms = 0.f;
-                    if (cudaEventElapsedTime(&ms, r.prof_ev[(size_t)it * 7 + k],
-                                             r.prof_ev[(size_t)it * 7 + k + 1]) == cudaSuccess) {
+                    const size_t e0 = (size_t)it * (LGK_K_COUNT + 1) + k;
+                    if (cudaEventElapsedTime(&ms, r.prof_ev[e0], r.prof_ev[e0 + 1]) == cudaSuccess) {
                         r.prof_ms[k] += ms;
                         r.prof_n[k] += 1;
                     } else {

@@ -59,20 +59,32 @@ struct TcMaps {
     CUtensorMap R1, rhs, V;   // hi/lo iterates, n_tile x 64 tiles
 };
 
+// Stream-K work plan of one tensor-core GEMM (device int arrays, see
+// build_plan): per CTA its segments, per segment (row tile, column tile,
+// k begin, k end, slot), per output tile the slots that cover it in k order.
+struct GemmPlan {
+    DevBuf buf;
+    int grid = 0, nseg = 0, rows = 0, col_tiles = 0, n_tile = 0;
+    const int* cta_seg = nullptr;
+    const int* seg = nullptr;
+    const int* tile_begin = nullptr;
+    const int* tile_slots = nullptr;
+};
+
 struct ResultData {
     std::shared_ptr<CaseData> cs;
     TcMaps maps;
-    bool maps_ready = false;
+    GemmPlan plan1, plan_s, plan2;    // GEMM1, solve, GEMM2
     int K = 0, Kp = 0, n_tile = 0, n_tile_s = 0;   // column tiles: GEMMs, solve
     double tol = 0.0;
     int max_iter = 0;
-    int splits1 = 1, splits_s = 1;         // split-K factors of GEMM1 and the solve
 
     DevBuf q1, q2;            // float [Kp][n_pad], [Kp][m_pad]
     DevBuf R1;                // FP32: float [Kp][n_pad]; BF16: bf16 [2][Kp][n_pad]
     DevBuf rhs, V;            // FP32: float [Kp][m_pad]; BF16: rhs bf16 [3][Kp][m_pad], V [2][Kp][m_pad]
     DevBuf W;                 // FP32 only: float [Kp][n_pad] (A^T V before its epilogue)
-    DevBuf part;              // float [splits][Kp][m_pad] split-K partial sums
+    DevBuf part;              // float segment partial sums [slot][n_tile][128] (BF16 forms), or
+                              // one GEMM output [Kp][rows] (FP32 form)
     DevBuf utab;              // float [Kp][n_slot] upper bounds u per slot
     DevBuf colp;              // float [4][Kp]: rho, 1/rho, w_BOT, unused
     DevBuf active, iters;     // int [Kp]
@@ -83,7 +95,7 @@ struct ResultData {
 
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
-    std::vector<cudaEvent_t> prof_ev;        // 7 per captured iteration (kernel boundaries)
+    std::vector<cudaEvent_t> prof_ev;        // LGK_K_COUNT + 1 per captured iteration
     double prof_ms[LGK_K_COUNT] = {0};
     long long prof_n[LGK_K_COUNT] = {0};
     ~ResultData();
@@ -107,7 +119,8 @@ int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
           double* C, int ldc);
 
 // Tensor-core GEMMs (tc_gemm.cu)
-int plan_splits(int kblocks, int row_tiles, int n_tiles);
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile);
+int sm_count();
 struct IterCtx;
 IterCtx make_ctx_public(ResultData& r);
 int tc_prepare(ResultData& r);  // attributes + TMA maps, before capture

@@ -6,7 +6,13 @@
 //   warps 2..5  epilogue: tcgen05.ld of the 128 x N accumulator, one row per thread
 //
 // Output tile: 128 rows of the long dimension (m for GEMM1 and the solve, n
-// for GEMM2) x N columns (weightings, N <= 256).  Each product A.B of the
+// for GEMM2) x N columns (weightings, N <= 256).  The kernel is persistent and
+// stream-K scheduled: the (tile, 64-wide k block) units of a GEMM are cut into
+// one contiguous run per CTA, so every SM streams the same number of operand
+// blocks; a run is split into segments at tile boundaries, each segment's
+// partial sum goes to its own slot (two TMEM accumulators, so the epilogue of
+// one segment overlaps the loads and MMAs of the next), and the reduce kernels
+// add a tile's slots in k order (deterministic).  Each product A.B of the
 // iteration is a sum of BF16 x BF16 terms (exact products, FP32 sums):
 //   GEMM1   A . R1         = A_hi.R1_hi + A_hi.R1_lo + A_lo.R1_hi  (3 terms; the
 //                            one-term-A form drops A_lo: 2 terms)
@@ -15,8 +21,6 @@
 //                            S^{-1} and rhs each split into three BF16 parts,
 //                            because S amplifies the rounding of its input)
 //   GEMM2   A^T . V        = A_hi^T.V_hi + A_hi^T.V_lo + A_lo^T.V_hi (3 or 2 terms)
-// GEMM1 and the solve write split-K partial sums; GEMM2 runs the q1 update
-// of the n-block (Eq. admm z- and y-steps in q-form) in its epilogue.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -108,6 +112,10 @@ __device__ inline void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, u
         : "memory");
 }
 
+__device__ inline void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ inline void tc_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -159,179 +167,147 @@ __host__ __device__ constexpr int term_b(int NT, int t) {
                                : (t == 0 || t == 2 || t == 5 ? 0 : (t == 1 || t == 4 ? 1 : 2));
 }
 
-enum { EPI_PARTIAL = 0, EPI_GEMM2 = 1 };
 
 struct TcArgs {
-    int kb_total;       // 64-wide k blocks of the contraction
-    int kb_per_split;   // k blocks per CTA along gridDim.z
-    int n_tile;         // columns per CTA (multiple of 16, <= 256)
-    int tmem_cols;      // power of two >= n_tile
+    const int* cta_seg;   // segments of CTA c: [cta_seg[c], cta_seg[c + 1])
+    const int* seg;       // 5 ints per segment: row tile, column tile, kb begin, kb end, slot
+    int n_tile;           // columns per tile (multiple of 16, <= 256)
+    int tmem_cols;        // columns of one accumulator (power of two >= n_tile); two of them
     int stages;
     int stage_bytes;
-    float* part;        // EPI_PARTIAL: [split][Kp][rows_pad]
-    int rows_pad;
+    float* part;          // [slot][n_tile][128] segment partial sums
 };
 
 constexpr int kThreads = 192;
 constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile
 
-template <int NA, int NB, int NT, bool A_MN, int EPI>
+template <int NA, int NB, int NT, bool A_MN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcArgs a, IterCtx cx) {
-    if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
+              TcArgs a, Control* ctrl) {
+    if (ctrl->n_active == 0 || ctrl->err) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = a.stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * a.stage_bytes);
-    // bars[0..S): full, [S..2S): empty, [2S]: accumulator ready
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 1);
-    float* ep_smem = reinterpret_cast<float*>(bars + 2 * S + 2);
+    // bars: [0, S) stage full, [S, 2S) stage empty, 2S + b accumulator b full,
+    // 2S + 2 + b accumulator b drained
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = blockIdx.x * 128;
-    const int col0 = blockIdx.y * a.n_tile;
-    const int split = blockIdx.z;
-    const int kb0 = split * a.kb_per_split;
-    const int kb1 = min(a.kb_total, kb0 + a.kb_per_split);
-    const int nkb = kb1 - kb0;
-    int* err = &cx.ctrl->err;
+    const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
+    int* err = &ctrl->err;
     const int b_bytes = a.n_tile * 128;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * S + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < 2 * S + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        mbar_init(smem_u32(&bars[2 * S + 2]), 4);     // one arrival per epilogue warp
+        mbar_init(smem_u32(&bars[2 * S + 3]), 4);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 2 * a.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0 && nkb > 0) {
-        // ---------------- TMA producer
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
-        for (int it = 0; it < nkb && ok; ++it) {
-            int s = it % S;
-            uint32_t ph = (uint32_t)(it / S) & 1u;
-            ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
-            if (!ok) break;
-            uint32_t full = smem_u32(&bars[s]);
-            uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-            mbar_expect_tx(full, (uint32_t)a.stage_bytes);
-            int kx = (kb0 + it) * 64;
-            if (A_MN) {
+        int it = 0;
+        for (int sg = s0; sg < s1 && ok; ++sg) {
+            const int* g = a.seg + 5 * sg;
+            const int row0 = g[0] * 128, col0 = g[1] * a.n_tile;
+            for (int kb = g[2]; kb < g[3] && ok; ++kb, ++it) {
+                const int s = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
+                if (!ok) break;
+                const uint32_t full = smem_u32(&bars[s]);
+                const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
+                mbar_expect_tx(full, (uint32_t)a.stage_bytes);
+                const int kx = kb * 64;
+                if (A_MN) {
 #pragma unroll
-                for (int p = 0; p < NA; ++p) {
-                    tma_load_3d(st + p * kABytes, &tmA, row0, kx, p, full);
-                    tma_load_3d(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full);
+                    for (int p = 0; p < NA; ++p) {
+                        tma_load_3d(st + p * kABytes, &tmA, row0, kx, p, full);
+                        tma_load_3d(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full);
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, &tmA, kx, row0, p, full);
                 }
-            } else {
+                const uint32_t sb = st + NA * kABytes;
 #pragma unroll
-                for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, &tmA, kx, row0, p, full);
+                for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &tmB, kx, col0, p, full);
             }
-            uint32_t sb = st + NA * kABytes;
-#pragma unroll
-            for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &tmB, kx, col0, p, full);
         }
         // drain: wait (bounded) for the copies of the last issued stages
-        int last = nkb;
-        for (int it = max(0, last - S); it < last && ok; ++it)
-            ok = mbar_wait(smem_u32(&bars[it % S]), (uint32_t)(it / S) & 1u, err);
-    } else if (warp == 1 && lane == 0 && nkb > 0) {
+        for (int j = max(0, it - S); j < it && ok; ++j)
+            ok = mbar_wait(smem_u32(&bars[j % S]), (uint32_t)(j / S) & 1u, err);
+    } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         const uint32_t idesc = instr_desc(a.n_tile, A_MN);
         bool ok = true;
-        for (int it = 0; it < nkb; ++it) {
-            int s = it % S;
-            uint32_t ph = (uint32_t)(it / S) & 1u;
-            if (ok) ok = mbar_wait(smem_u32(&bars[s]), ph, err);
+        int it = 0;
+        for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
+            const int* g = a.seg + 5 * sg;
+            const int b = u & 1;
+            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 2 + b]), (uint32_t)((u >> 1) & 1) ^ 1u, err);
             tc_fence_after();
-            uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-            uint32_t sb = st + NA * kABytes;
-            if (ok) {
+            const uint32_t d = tmem + (uint32_t)(b * a.tmem_cols);
+            for (int kb = g[2]; kb < g[3]; ++kb, ++it) {
+                const int s = it % S;
+                const uint32_t ph = (uint32_t)(it / S) & 1u;
+                if (ok) ok = mbar_wait(smem_u32(&bars[s]), ph, err);
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
+                const uint32_t sb = st + NA * kABytes;
+                if (ok) {
 #pragma unroll
-                for (int t = 0; t < NT; ++t) {
-                    const uint32_t sa = st + term_a(NT, t) * kABytes;
-                    const uint32_t sbt = sb + term_b(NT, t) * b_bytes;
+                    for (int t = 0; t < NT; ++t) {
+                        const uint32_t sa = st + term_a(NT, t) * kABytes;
+                        const uint32_t sbt = sb + term_b(NT, t) * b_bytes;
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
-                                           : smem_desc(sa + ks * 32, 16, 1024);
-                        uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
-                        tc_mma(tmem, ad, bd, idesc, (it > 0 || t > 0 || ks > 0) ? 1u : 0u);
-                    }
-                }
-            }
-            tc_commit(smem_u32(&bars[S + s]));      // frees the stage when the MMAs are done
-        }
-        tc_commit(smem_u32(&bars[2 * S]));          // accumulator complete
-    } else if (warp >= 2) {
-        // ---------------- epilogue
-        const int ew = warp & 3;                    // TMEM lane quarter of this warp
-        const int row = row0 + ew * 32 + lane;
-        const int et = threadIdx.x - 64;            // 0..127
-        bool ok = nkb > 0 && mbar_wait(smem_u32(&bars[2 * S]), 0u, err);
-        tc_fence_after();
-        if (EPI == EPI_PARTIAL) {
-            float* out = a.part + ((size_t)split * cx.Kp + col0) * a.rows_pad + row;
-            for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj)
-                    out[(size_t)(c0 + jj) * a.rows_pad] = ok ? v[jj] : 0.f;
-            }
-        } else {
-            // GEMM2 epilogue: q1 update of the n-block for this row p = row
-            const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
-            float* acc = ep_smem;                   // [n_tile][5] residual sums
-            for (int e = et; e < a.n_tile * 5; e += 128) acc[e] = 0.f;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const int p = row;
-            const int sl = cx.col_slot[p];
-            const float c = cx.c_slot[sl];
-            __nv_bfloat16* R1 = reinterpret_cast<__nv_bfloat16*>(a.part);   // R1 hi/lo buffer
-            for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = col0 + c0 + jj;
-                    const size_t o = (size_t)j * cx.n_pad + p;
-                    const float u = cx.utab[j * cx.n_slot + sl];
-                    const float cr = c * cx.inv_rho[j];
-                    Q1Update q = q1_update(cx.q1[o], ok ? v[jj] : 0.f, u, cr);
-                    if (cx.active[j]) cx.q1[o] = q.qn;
-                    __nv_bfloat16 hi, lo;
-                    split_bf16(q.r1, hi, lo);
-                    R1[o] = hi;
-                    R1[(size_t)cx.Kp * cx.n_pad + o] = lo;
-                    if (check) {
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            float s = q.res[k];
-#pragma unroll
-                            for (int of = 16; of > 0; of >>= 1) s += __shfl_xor_sync(0xffffffffu, s, of);
-                            if (lane == 0) atomicAdd(&acc[(c0 + jj) * 5 + k], s);
+                        for (int ks = 0; ks < 4; ++ks) {
+                            uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
+                                               : smem_desc(sa + ks * 32, 16, 1024);
+                            uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
+                            tc_mma(d, ad, bd, idesc, (kb > g[2] || t > 0 || ks > 0) ? 1u : 0u);
                         }
                     }
                 }
+                tc_commit(smem_u32(&bars[S + s]));      // frees the stage when its MMAs finish
             }
-            if (check) {
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int e = et; e < a.n_tile * 5; e += 128) {
-                    int jj = e / 5, k = e % 5;
-                    cx.resid[((size_t)blockIdx.x * cx.Kp + col0 + jj) * 5 + k] = (double)acc[e];
-                }
+            tc_commit(smem_u32(&bars[2 * S + b]));      // accumulator b complete
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: accumulator -> segment slot
+        const int ew = warp & 3;                        // TMEM lane quarter of this warp
+        const int r = ew * 32 + lane;                   // row within the tile
+        bool ok = true;
+        for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
+            const int b = u & 1;
+            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u >> 1) & 1), err);
+            tc_fence_after();
+            float* out = a.part + (size_t)a.seg[5 * sg + 4] * a.n_tile * 128 + r;
+            const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(b * a.tmem_cols);
+            for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
+                float v[16];
+                tmem_ld16(base + (uint32_t)c0, v);
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) out[(size_t)(c0 + jj) * 128] = ok ? v[jj] : 0.f;
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 2 + b]));
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, a.tmem_cols);
+        tmem_dealloc(tmem, 2 * a.tmem_cols);
     }
 }
 
@@ -366,8 +342,8 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
     cuuint64_t strides[2] = {cols * 2, cols * rows * 2};
     cuuint32_t box[3] = {64, box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
-                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r));
@@ -378,38 +354,89 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
 
 static constexpr int kSmemLimit = 232448;    // 227 KB opt-in per block
 
-static int smem_extra(int n_tile) { return 1024 + 8 * 20 + 16 + n_tile * 5 * 4; }
+static int smem_extra() { return 1024 + 8 * (2 * 8 + 4) + 16; }
 
-template <int NA, int NB, int NT, bool A_MN, int EPI>
-static int launch(const CUtensorMap& mA, const CUtensorMap& mB, TcArgs a, const IterCtx& cx,
-                  dim3 grid, cudaStream_t st) {
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    }
+    return n;
+}
+
+// Stream-K plan: the units (column tile, row tile, k block), in that order,
+// cut into `grid` contiguous runs of equal length (+-1), each run split into
+// segments at tile boundaries.  Depends only on the GEMM's shape.
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile) {
+    const long long U = (long long)rows * col_tiles * kb_total;
+    const int grid = (int)std::min<long long>(sm_count(), U);
+    std::vector<int> cta_seg(grid + 1), seg, tile_begin(rows * col_tiles + 1, 0);
+    std::vector<std::vector<int>> per_tile(rows * col_tiles);
+    int nseg = 0;
+    for (int c = 0; c < grid; ++c) {
+        cta_seg[c] = nseg;
+        long long u0 = U * c / grid, u1 = U * (c + 1) / grid;
+        while (u0 < u1) {
+            long long tile = u0 / kb_total;
+            int kb0 = (int)(u0 % kb_total);
+            int kb1 = (int)std::min<long long>(kb_total, kb0 + (u1 - u0));
+            int ct = (int)(tile / rows), rt = (int)(tile % rows);
+            seg.insert(seg.end(), {rt, ct, kb0, kb1, nseg});
+            per_tile[tile].push_back(nseg);
+            ++nseg;
+            u0 += kb1 - kb0;
+        }
+    }
+    cta_seg[grid] = nseg;
+    std::vector<int> tile_slots;
+    for (size_t t = 0; t < per_tile.size(); ++t) {
+        tile_begin[t] = (int)tile_slots.size();
+        tile_slots.insert(tile_slots.end(), per_tile[t].begin(), per_tile[t].end());
+    }
+    tile_begin[per_tile.size()] = (int)tile_slots.size();
+    std::vector<int> all;
+    all.insert(all.end(), cta_seg.begin(), cta_seg.end());
+    all.insert(all.end(), seg.begin(), seg.end());
+    all.insert(all.end(), tile_begin.begin(), tile_begin.end());
+    all.insert(all.end(), tile_slots.begin(), tile_slots.end());
+    int rc;
+    if ((rc = P.buf.alloc(all.size() * 4))) return rc;
+    LGK_CUDA_TRY(cudaMemcpy(P.buf.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
+    const int* d = P.buf.as<int>();
+    P.grid = grid;
+    P.nseg = nseg;
+    P.rows = rows;
+    P.col_tiles = col_tiles;
+    P.n_tile = n_tile;
+    P.cta_seg = d;
+    P.seg = d + grid + 1;
+    P.tile_begin = d + grid + 1 + 5 * nseg;
+    P.tile_slots = P.tile_begin + rows * col_tiles + 1;
+    return LGK_OK;
+}
+
+template <int NA, int NB, int NT, bool A_MN>
+static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, float* part,
+                  Control* ctrl, cudaStream_t st) {
+    TcArgs a{};
+    a.cta_seg = P.cta_seg;
+    a.seg = P.seg;
+    a.n_tile = P.n_tile;
+    a.part = part;
     a.stage_bytes = NA * kABytes + NB * a.n_tile * 128;
-    int extra = smem_extra(a.n_tile);
-    a.stages = std::min(8, (kSmemLimit - extra) / a.stage_bytes);
+    a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
     if (a.stages < 2) {
         set_error("tensor-core GEMM: stage does not fit in shared memory");
         return LGK_EINVAL;
     }
     a.tmem_cols = 32;
     while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
-    size_t smem = (size_t)a.stages * a.stage_bytes + extra;
-    auto kern = k_tc_gemm<NA, NB, NT, A_MN, EPI>;
-    kern<<<grid, kThreads, smem, st>>>(mA, mB, a, cx);
+    size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
+    k_tc_gemm<NA, NB, NT, A_MN><<<P.grid, kThreads, smem, st>>>(mA, mB, a, ctrl);
     LGK_LAUNCH_CHECK();
     return LGK_OK;
-}
-
-// split-K factor: enough CTAs to cover the SMs about once, every split at
-// least 4 k blocks; independent of K so a column's sums never depend on the
-// batch it is solved in.
-int plan_splits(int kblocks, int row_tiles, int n_tiles) {
-    (void)n_tiles;
-    int s = std::max(1, 148 / std::max(1, row_tiles));
-    s = std::min(s, std::max(1, kblocks / 4));
-    // make every split non-empty
-    int per = (kblocks + s - 1) / s;
-    s = (kblocks + per - 1) / per;
-    return s;
 }
 
 static int maps_for(ResultData& r, TcMaps& M) {
@@ -424,16 +451,9 @@ static int maps_for(ResultData& r, TcMaps& M) {
     return LGK_OK;
 }
 
-static int ensure_maps(ResultData& r) {
-    if (r.maps_ready) return LGK_OK;
-    int rc = maps_for(r, r.maps);
-    r.maps_ready = rc == LGK_OK;
-    return rc;
-}
-
-template <int NA, int NB, int NT, bool A_MN, int EPI>
+template <int NA, int NB, int NT, bool A_MN>
 static int set_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -442,61 +462,42 @@ static int set_smem_attr() {
     return LGK_OK;
 }
 
-// Outside any stream capture: kernel attributes and the TMA descriptors.
+// Outside any stream capture: kernel attributes, TMA descriptors, plans.
 int tc_prepare(ResultData& r) {
+    CaseData& cs = *r.cs;
     int rc;
-    if ((rc = set_smem_attr<1, 2, 2, false, EPI_PARTIAL>())) return rc;
-    if ((rc = set_smem_attr<2, 2, 3, false, EPI_PARTIAL>())) return rc;
-    if ((rc = set_smem_attr<3, 3, 6, false, EPI_PARTIAL>())) return rc;
-    if ((rc = set_smem_attr<1, 2, 2, true, EPI_GEMM2>())) return rc;
-    if ((rc = set_smem_attr<2, 2, 3, true, EPI_GEMM2>())) return rc;
-    return ensure_maps(r);
+    if ((rc = set_smem_attr<1, 2, 2, false>())) return rc;
+    if ((rc = set_smem_attr<2, 2, 3, false>())) return rc;
+    if ((rc = set_smem_attr<3, 3, 6, false>())) return rc;
+    if ((rc = set_smem_attr<1, 2, 2, true>())) return rc;
+    if ((rc = set_smem_attr<2, 2, 3, true>())) return rc;
+    if ((rc = maps_for(r, r.maps))) return rc;
+    const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
+    if ((rc = build_plan(r.plan1, mt, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile))) return rc;
+    if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s))) return rc;
+    if ((rc = build_plan(r.plan2, nt, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile))) return rc;
+    size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile, (size_t)r.plan_s.nseg * r.n_tile_s,
+                             (size_t)r.plan2.nseg * r.n_tile});
+    return r.part.alloc(slots * 128 * 4);
 }
 
 int tc_gemm1(ResultData& r) {
-    int rc;
-    if ((rc = ensure_maps(r))) return rc;
     CaseData& cs = *r.cs;
-    TcArgs a{};
-    a.kb_total = cs.n_pad / 64;
-    a.kb_per_split = (a.kb_total + r.splits1 - 1) / r.splits1;
-    a.n_tile = r.n_tile;
-    a.part = r.part.as<float>();
-    a.rows_pad = cs.m_pad;
-    dim3 grid(cs.m_pad / 128, r.Kp / r.n_tile, r.splits1);
     if (cs.na == 2)
-        return launch<2, 2, 3, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, a, make_ctx_public(r), grid, cs.stream);
-    return launch<1, 2, 2, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, a, make_ctx_public(r), grid, cs.stream);
+        return launch<2, 2, 3, false>(r.maps.A_k, r.maps.R1, r.plan1, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
+    return launch<1, 2, 2, false>(r.maps.A_k, r.maps.R1, r.plan1, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
 }
 
 int tc_solve(ResultData& r) {
-    int rc;
-    if ((rc = ensure_maps(r))) return rc;
     CaseData& cs = *r.cs;
-    TcArgs a{};
-    a.kb_total = cs.m_pad / 64;
-    a.kb_per_split = (a.kb_total + r.splits_s - 1) / r.splits_s;
-    a.n_tile = r.n_tile_s;
-    a.part = r.part.as<float>();
-    a.rows_pad = cs.m_pad;
-    dim3 grid(cs.m_pad / 128, r.Kp / r.n_tile_s, r.splits_s);
-    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, a, make_ctx_public(r), grid, cs.stream);
+    return launch<3, 3, 6, false>(r.maps.G3, r.maps.rhs, r.plan_s, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
 }
 
 int tc_gemm2(ResultData& r) {
-    int rc;
-    if ((rc = ensure_maps(r))) return rc;
     CaseData& cs = *r.cs;
-    TcArgs a{};
-    a.kb_total = cs.m_pad / 64;
-    a.kb_per_split = a.kb_total;
-    a.n_tile = r.n_tile;
-    a.part = reinterpret_cast<float*>(r.R1.p);      // epilogue output: R1 hi/lo
-    a.rows_pad = cs.n_pad;
-    dim3 grid(cs.n_pad / 128, r.Kp / r.n_tile, 1);
     if (cs.na == 2)
-        return launch<2, 2, 3, true, EPI_GEMM2>(r.maps.A_mn, r.maps.V, a, make_ctx_public(r), grid, cs.stream);
-    return launch<1, 2, 2, true, EPI_GEMM2>(r.maps.A_mn, r.maps.V, a, make_ctx_public(r), grid, cs.stream);
+        return launch<2, 2, 3, true>(r.maps.A_mn, r.maps.V, r.plan2, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
+    return launch<1, 2, 2, true>(r.maps.A_mn, r.maps.V, r.plan2, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
 }
 
 }  // namespace lgk

@@ -223,7 +223,7 @@ def fetch_state(res: Result):
     return q1, q2
 
 
-KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "finalize")
+KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "q1_update", "finalize")
 
 
 def fetch_profile(res: Result) -> dict:

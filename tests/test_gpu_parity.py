@@ -48,7 +48,7 @@ def cfg0():
     lp = L.precondition(L.assemble_case(case))
     W = SC.slider_weights(3)
     b, l, u = L.bounds(lp, W)
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     opt = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(W.shape[0])])
     ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=TOL)
     pts, label, _ = SC.eval_grid(case, spacing=1.0, margin=12.0)
@@ -195,7 +195,7 @@ def test_ragged_batch_and_degenerate_columns(lgk, cfg0):
     W[3, 1] = 0.0
     W[3, 2] = 0.0
     W[5, 2] = 0.0
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     cs = make(lgk, c["case"], 2)
     res = lgk.solve_weightings(cs, W, rho, tol=5e-5, max_iter=40000)
     st = lgk.fetch_stats(res)
@@ -214,7 +214,8 @@ def test_rho_rule_inside_library(lgk, cfg0):
     c = cfg0
     cs = make(lgk, c["case"], 2)
     a = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=20)
-    b = lgk.solve_weightings(cs, c["W"], None, w0_bot=SC.W0_BOT, rho0=L.RHO0, tol=0.0, max_iter=20)
+    b = lgk.solve_weightings(cs, c["W"], None, w0_bot=SC.W0_BOT, rho0=L.rho0_for(c["lp"]),
+                             tol=0.0, max_iter=20)
     za, _ = lgk.fetch_state(a)
     zb, _ = lgk.fetch_state(b)
     np.testing.assert_allclose(za, zb, rtol=1e-6, atol=1e-12)

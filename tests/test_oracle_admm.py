@@ -31,7 +31,7 @@ def test_admm_reaches_simplex_optimum_on_small_case():
     W = SC.slider_weights(2)
     b, l, u = L.bounds(lp, W)
     v = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(4)])
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, 2.5e3)   # fixed rho0: this pins convergence, not the rule
     early = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=3000)
     res = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=60000)
     err_early = np.abs(early.objective(lp.c) - v) / np.abs(v)
@@ -46,7 +46,7 @@ def test_admm_cfg0_objective_gap_and_invariants(cfg0):
     (|obj - obj*| / max(1, |obj*|)); z1 in [l, u], z2 <= b and y2 >= 0 hold
     exactly (projections)."""
     case, lp, W, b, l, u, opt = cfg0
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     res = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=1e-4)
     assert res.converged.all()
     gap = np.abs(res.objective(lp.c) - opt) / np.maximum(1.0, np.abs(opt))
@@ -59,7 +59,7 @@ def test_admm_cfg0_objective_gap_and_invariants(cfg0):
 
 def test_fixed_iteration_mode_and_column_independence(cfg0):
     case, lp, W, b, l, u, opt = cfg0
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     full = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=40)
     assert np.all(full.iters == 40)
     one = AD.admm(lp.A, lp.c, b[:, 4:5], l[:, 4:5], u[:, 4:5], rho[4:5], max_iter=40)
@@ -76,7 +76,7 @@ def test_q_form_recurrence_equals_literal_admm(cfg0):
     import scipy.linalg
     case, lp, W, b, l, u, opt = cfg0
     A = lp.A
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     n_it = 50
     lit = AD.admm(A, lp.c, b, l, u, rho, max_iter=n_it)
     cf = scipy.linalg.cho_factor(A @ A.T + np.eye(A.shape[0]), lower=True)
@@ -102,7 +102,7 @@ def test_admm_multipliers_give_primal_times(cfg0):
     gives reach the optimal planning objective within the stop tolerance."""
     from oracle import kkt as KK
     case, lp, W, b, l, u, opt = cfg0
-    rho = L.rho_rule(W[:, 3], SC.W0_BOT)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     res = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=1e-5)
     lam = res.multipliers()
     for j in range(W.shape[0]):

@@ -186,9 +186,11 @@ def test_preprocessing_keeps_optimum(cfg0):
 
 
 def test_rho_rule_and_beta():
-    assert L.rho_rule(1e-4, 1e-4) == pytest.approx(L.RHO0)
-    assert L.rho_rule(1e-2, 1e-4) == pytest.approx(L.RHO0 * 0.1)
+    assert L.rho_rule(1e-4, 1e-4, 7.0) == pytest.approx(7.0)
+    assert L.rho_rule(1e-2, 1e-4, 7.0) == pytest.approx(0.7)
     assert L.rho_rule(4e-4, 1e-4, rho0=L.RHO0_PAPER) == pytest.approx(1.25e-3)
+    lp = L.precondition(tiny_case(0)[2])
+    assert L.rho0_for(lp) == pytest.approx(L.RHO0_PER_BETA * lp.beta)
 
 
 def test_multitarget_bounds():
