@@ -159,6 +159,41 @@ int lgk_fetch_times(const lgk_result* res, double* t, double* tau);
  * (host), dose is K x n_eval (host).  Computed on the device in FP64. */
 int lgk_fetch_doses(const lgk_result* res, const double* phi_eval, int n_eval, double* dose);
 
+/*
+ * lgk_fetch_doses_device -- allocation-free variant of lgk_fetch_doses.
+ *
+ * For callers that must not allocate device memory at run time: code whose
+ * device memory is owned by another framework's pool or a fixed arena,
+ * real-time loops that cannot afford an allocator's latency or its implicit
+ * device synchronisation, and callers that have reserved all of the GPU's
+ * memory up front.  Such callers pass their own device buffers and this call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ * The paper has no counterpart of this entry point; it is a convenience of
+ * this library.
+ *
+ * Computes dose = phi_eval t exactly as lgk_fetch_doses does (FP64, same
+ * kernel), for the K plans of `res`:
+ *   phi_eval_dev  DEVICE pointer, n_eval x 24N FP64 row-major, on the case's
+ *                 device (checked; host or other-device pointers are rejected)
+ *   dose_dev      DEVICE pointer, K x n_eval FP64 row-major, written
+ * The plans' sector times (K x 24N FP64) are staged in a scratch array that
+ * the library keeps in static device memory: LGK_NOALLOC_MAX_TIMES doubles
+ * (32 MiB), held on every GPU that loads the library until the process exits.
+ * K x 24N above that limit returns LGK_EINVAL (split the plans into smaller
+ * batches).  Every element of the scratch that is read is first written by
+ * the same call, so nothing carries over from one call to the next; but all
+ * calls share the one array, so calls that overlap on the GPU (from several
+ * host threads, or on several streams) race with each other and must be
+ * serialised by the caller.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device); make that first call before any stream capture.
+ * Runs on the case's stream and returns when the doses are written.
+ * Errors: LGK_EINVAL, LGK_ECUDA.
+ */
+#define LGK_NOALLOC_MAX_TIMES (1 << 22)
+int lgk_fetch_doses_device(const lgk_result* res, const double* phi_eval_dev, int n_eval,
+                           double* dose_dev);
+
 /* Per-column statistics (each pointer may be NULL; arrays of K):
  * iterations run, dual objective c^T z1 (FP64 on the device), relative primal
  * and dual residuals at the last test, converged flag. */

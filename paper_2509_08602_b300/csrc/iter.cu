@@ -588,6 +588,25 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     return LGK_OK;
 }
 
+// Sector times t = D_r rho max(q2 - b, 0) on the beam rows, FP64, K x B, into
+// caller-provided device memory (the allocation-free dose entry point).
+__global__ void k_times_into(IterCtx cx, int K, double* t) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= cx.n_beams || j >= K) return;
+    double q = cx.q2[(size_t)j * cx.m_pad + i];
+    t[(size_t)j * cx.n_beams + i] = cx.Dr[i] * (double)cx.rho[j] * fmax(q, 0.0);
+}
+
+int times_into(const ResultData& r, double* t_dev) {
+    ResultData& rr = const_cast<ResultData&>(r);
+    CaseData& cs = *rr.cs;
+    IterCtx cx = make_ctx(rr);
+    dim3 g((cs.n_beams + 255) / 256, r.K);
+    k_times_into<<<g, 256, 0, cs.stream>>>(cx, r.K, t_dev);
+    LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
 // ------------------------------------------------------------------ fetch
 
 int fetch_times(const ResultData& r, double* t, double* tau) {

@@ -112,6 +112,7 @@ int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double*
 int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri,
                 double* rel_dual, uint8_t* converged);
 int fetch_state(const ResultData& r, double* q1, double* q2);
+int times_into(const ResultData& r, double* t_dev);   // K x n_beams FP64, device
 
 // FP64 GEMM (setup.cu):  C = alpha op(A) op(B) + beta C, row-major.
 int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,

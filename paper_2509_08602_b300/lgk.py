@@ -19,6 +19,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "liblgk.so"
 PREC_FP32 = 0
 PREC_BF16 = 1
 PREC_BF16X3 = 2
+LGK_NOALLOC_MAX_TIMES = 1 << 22     # doubles of static scratch for lgk_fetch_doses_device
 STATUS = {0: "LGK_OK", 1: "LGK_EINVAL", 2: "LGK_ENOMEM", 3: "LGK_EBUDGET", 4: "LGK_ENOTPD",
           5: "LGK_ECUDA", 6: "LGK_ETIMEOUT"}
 
@@ -64,6 +65,8 @@ def _load():
                                               C.c_double, C.c_double, C.c_double, C.c_int,
                                               P(C.c_double), P(C.c_double), P(C.c_void_p)]
     lib.lgk_fetch_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_longlong)]
+    lib.lgk_fetch_doses_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+    lib.lgk_fetch_doses_device.restype = C.c_int
     lib.lgk_free_result.argtypes = [C.c_void_p]
     lib.lgk_destroy_case.argtypes = [C.c_void_p]
     lib.lgk_last_error.restype = C.c_char_p
@@ -202,6 +205,14 @@ def fetch_doses(res: Result, phi_eval) -> np.ndarray:
     _check(_lib.lgk_fetch_doses(res._h, _ptr(phi_eval, C.c_double), int(phi_eval.shape[0]),
                                 _ptr(dose, C.c_double)))
     return dose
+
+
+def fetch_doses_device(res: Result, phi_eval_ptr: int, n_eval: int, dose_ptr: int) -> None:
+    """Allocation-free dose evaluation on caller device buffers (integer device
+    addresses, e.g. torch's data_ptr()): phi_eval n_eval x 24N FP64 in,
+    dose K x n_eval FP64 out.  See lgk_fetch_doses_device in include/lgk.h."""
+    _check(_lib.lgk_fetch_doses_device(res._h, C.c_void_p(phi_eval_ptr), int(n_eval),
+                                       C.c_void_p(dose_ptr)))
 
 
 def fetch_stats(res: Result) -> dict:
