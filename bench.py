@@ -51,10 +51,10 @@ def peaks():
 
 def kernel_work(name, m, n, K):
     """Algorithmic (bytes, flops) of one launch of an iteration kernel."""
-    if name == "gemm1":      # A . R1: A as 2 bf16 terms once, R1 hi/lo, rhs out
-        return 4 * m * n + 4 * n * K + 4 * m * K, 2 * m * n * K
-    if name == "solve":      # S^{-1} . rhs: S^{-1} as 3 bf16 parts, rhs 3 parts, v out
-        return 6 * m * m + 6 * m * K + 4 * m * K, 2 * m * m * K
+    if name == "gemm1":      # A . R1 (A as 2 bf16 terms once, R1 hi/lo) + rhs step: q2 in, rhs 3 terms out
+        return 4 * m * n + 4 * n * K + 10 * m * K, 2 * m * n * K
+    if name == "solve":      # S^{-1} . rhs (3 bf16 parts each) + q2 update: q2 r/w, V hi/lo out
+        return 6 * m * m + 6 * m * K + 12 * m * K, 2 * m * m * K
     if name == "gemm2":      # A^T . V + q1 update: A (2 terms) once, V hi/lo, q1 r/w, R1 out
         return 4 * m * n + 4 * m * K + 12 * n * K, 2 * m * n * K
     if name in ("reduce_rhs", "reduce_solve"):

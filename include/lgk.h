@@ -217,7 +217,9 @@ int lgk_solve_weightings_warm(lgk_case* cs, int K, const double* W, const double
  * back to lgk_solve_weightings_warm resumes the iteration. */
 int lgk_fetch_state(const lgk_result* res, double* q1, double* q2);
 
-/* Kernel classes of one ADMM iteration, in launch order. */
+/* Kernel classes of one ADMM iteration, in launch order.  The BF16 forms run
+ * the q1 update inside the tensor-core GEMM2's epilogue (LGK_K_Q1_UPDATE
+ * reports zero launches for them); the FP32 form launches all seven. */
 enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLVE = 3,
        LGK_K_GEMM2 = 4, LGK_K_Q1_UPDATE = 5, LGK_K_FINALIZE = 6, LGK_K_COUNT = 7 };
 

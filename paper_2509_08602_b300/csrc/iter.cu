@@ -43,7 +43,7 @@ static void prof_mark(ResultData& r, int it, int k) {
     // External: captured as an event-record node of the graph (a plain record
     // inside a capture only expresses a dependency)
     if (!r.prof_ev.empty())
-        cudaEventRecordWithFlags(r.prof_ev[(size_t)it * (LGK_K_COUNT + 1) + k], r.cs->stream,
+        cudaEventRecordWithFlags(r.prof_ev[(size_t)it * (r.prof_class.size() + 1) + k], r.cs->stream,
                                  cudaEventRecordExternal);
 }
 
@@ -58,19 +58,36 @@ struct SumSrc {
     int rows_pad, row_tiles, n_tile;
 };
 
+// Sum of the GEMM output at (i, j): the plain matrix, or the tile's slots.
+// Slots of a tile are contiguous ([tile_begin[t], tile_begin[t + 1])), so the
+// loads of the different slots are independent of each other.
 __device__ inline float gemm_out(const SumSrc& s, int i, int j) {
     if (!s.tile_begin) return s.part[(size_t)j * s.rows_pad + i];
-    const int rt = i >> 7, ii = i & 127, ct = j / s.n_tile, jj = j - ct * s.n_tile;
-    const int t = ct * s.row_tiles + rt;
+    const int ct = j / s.n_tile, t = ct * s.row_tiles + (i >> 7);
+    const int b = __ldg(s.tile_begin + t), e = __ldg(s.tile_begin + t + 1);
+    const float* p = s.part + ((size_t)b * s.n_tile + (j - ct * s.n_tile)) * 128 + (i & 127);
+    const size_t stride = (size_t)s.n_tile * 128;
     float acc = 0.f;
-    for (int k = s.tile_begin[t]; k < s.tile_begin[t + 1]; ++k)
-        acc += s.part[((size_t)s.tile_slots[k] * s.n_tile + jj) * 128 + ii];
+    int k = 0;
+    for (; k + 4 <= e - b; k += 4) {
+        const float a0 = __ldcg(p + k * stride), a1 = __ldcg(p + (k + 1) * stride);
+        const float a2 = __ldcg(p + (k + 2) * stride), a3 = __ldcg(p + (k + 3) * stride);
+        acc += a0;
+        acc += a1;
+        acc += a2;
+        acc += a3;
+    }
+    for (; k < e - b; ++k) acc += __ldcg(p + k * stride);
     return acc;
 }
 
-// block-wide sum of 5 values into out[0..4] (thread 0 holds the result)
+// Element-wise kernels over the m-block (one element per thread, grid
+// (m_pad / 256, Kp)) or the n-block; kCols is the column group of the
+// residual partials written per 128-row tile.
+constexpr int kCols = 8;
+
 __device__ inline void block_sum5(float v[5], double* out) {
-    __shared__ float red[5][32];
+    __shared__ float red[5][8];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -111,20 +128,19 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
     }
 }
 
-// rhs = A R1 + q2 - 2 P2(q2)
+// rhs = A R1 + q2 - 2 P2(q2).  Grid (m_pad / 128, Kp), 128 threads.
 template <bool BF16>
-__global__ void k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
+__global__ void __launch_bounds__(128) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i >= cx.m_pad) return;
-    size_t o = (size_t)j * cx.m_pad + i;
+    const int i = blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
+    const size_t o = (size_t)j * cx.m_pad + i;
     const float acc = gemm_out(src, i, j);
-    float q = cx.q2[o];
-    float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
-    float r = acc + q - 2.f * p2;
+    const float q = cx.q2[o];
+    const float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
+    const float r = acc + q - 2.f * p2;
     if (BF16) {      // three BF16 parts: the solve amplifies input rounding
-        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(rhs);
         const size_t plane = (size_t)cx.Kp * cx.m_pad;
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(rhs);
         __nv_bfloat16 hi = __float2bfloat16_rn(r);
         float r1 = r - __bfloat162float(hi);
         __nv_bfloat16 mid = __float2bfloat16_rn(r1);
@@ -136,127 +152,145 @@ __global__ void k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
     }
 }
 
-// v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block.
+// v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block (one
+// per 128-row tile and column).  Grid (m_pad / 128, Kp), 128 threads.
 template <bool BF16>
-__global__ void k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
+__global__ void __launch_bounds__(128) k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
-    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (i < cx.m_pad) {
-        size_t o = (size_t)j * cx.m_pad + i;
-        const float v = gemm_out(src, i, j);
-        float qo = cx.q2[o];
-        float bb = b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
-        float zo = fminf(qo, bb);
-        float qn = v + zo;
-        if (cx.active[j]) cx.q2[o] = qn;
-        if (BF16) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(v, hi, lo);
-            static_cast<__nv_bfloat16*>(V)[o] = hi;
-            static_cast<__nv_bfloat16*>(V)[(size_t)cx.Kp * cx.m_pad + o] = lo;
-        } else {
-            static_cast<float*>(V)[o] = v;
-        }
-        if (check) {
-            float yo = qo - zo, zn = fminf(qn, bb), yn = qn - zn;
-            float r = yn - yo, x = qn - yo, s = zn - zo;
-            res[0] = r * r; res[1] = x * x; res[2] = zn * zn; res[3] = s * s; res[4] = yn * yn;
-        }
+    const int rt = blockIdx.x, i = rt * 128 + threadIdx.x, j = blockIdx.y;
+    const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
+    const size_t o = (size_t)j * cx.m_pad + i;
+    const float v = gemm_out(src, i, j);
+    const float qo = cx.q2[o];
+    const float bb = b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
+    const float zo = fminf(qo, bb);
+    const float qn = v + zo;
+    if (cx.active[j]) cx.q2[o] = qn;
+    if (BF16) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(v, hi, lo);
+        static_cast<__nv_bfloat16*>(V)[o] = hi;
+        static_cast<__nv_bfloat16*>(V)[(size_t)cx.Kp * cx.m_pad + o] = lo;
+    } else {
+        static_cast<float*>(V)[o] = v;
     }
     if (check) {
+        const float yo = qo - zo, zn = fminf(qn, bb), yn = qn - zn;
+        const float r = yn - yo, x = qn - yo, s = zn - zo;
+        float res[5] = {r * r, x * x, zn * zn, s * s, yn * yn};
         __shared__ double out[5];
         block_sum5(res, out);
         if (threadIdx.x == 0) {
-            double* dst = cx.resid + ((size_t)(cx.n_resid_n + blockIdx.x) * cx.Kp + j) * 5;
+            double* dst = cx.resid + ((size_t)(cx.n_resid_n + rt) * cx.Kp + j) * 5;
             for (int k = 0; k < 5; ++k) dst[k] = out[k];
         }
     }
 }
 
 // q1' = P1(q1) - c/rho - W and R1' = 2 P1(q1') - q1' - c/rho from W = A^T V;
-// residual partials of the n-block.  R1 is FP32 (FP32 form) or two BF16
-// terms (BF16 forms).
+// residual partials of the n-block (one per 128-row tile and column).  The
+// FP32 form's step after its cuBLAS GEMM2 (the BF16 forms run it in the
+// tensor-core GEMM2 epilogue).  Grid (n_pad / 128, Kp), 128 threads.
 template <bool BF16>
-__global__ void k_q1_update(IterCtx cx, SumSrc src, void* R1) {
+__global__ void __launch_bounds__(128) k_q1_update(IterCtx cx, SumSrc src, void* R1) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
-    float res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (p < cx.n_pad) {
-        size_t o = (size_t)j * cx.n_pad + p;
-        int sl = cx.col_slot[p];
-        float u = cx.utab[j * cx.n_slot + sl];
-        float cr = cx.c_slot[sl] * cx.inv_rho[j];
-        Q1Update q = q1_update(cx.q1[o], gemm_out(src, p, j), u, cr);
-        if (cx.active[j]) cx.q1[o] = q.qn;
-        if (BF16) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(q.r1, hi, lo);
-            static_cast<__nv_bfloat16*>(R1)[o] = hi;
-            static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
-        } else {
-            static_cast<float*>(R1)[o] = q.r1;
-        }
-        if (check)
-            for (int k = 0; k < 5; ++k) res[k] = q.res[k];
+    const int rt = blockIdx.x, p = rt * 128 + threadIdx.x, j = blockIdx.y;
+    const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
+    const size_t o = (size_t)j * cx.n_pad + p;
+    const int sl = cx.col_slot[p];
+    Q1Update q = q1_update(cx.q1[o], gemm_out(src, p, j), cx.utab[j * cx.n_slot + sl],
+                           cx.c_slot[sl] * cx.inv_rho[j]);
+    if (cx.active[j]) cx.q1[o] = q.qn;
+    if (BF16) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(q.r1, hi, lo);
+        static_cast<__nv_bfloat16*>(R1)[o] = hi;
+        static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
+    } else {
+        static_cast<float*>(R1)[o] = q.r1;
     }
     if (check) {
         __shared__ double out[5];
-        block_sum5(res, out);
+        block_sum5(q.res, out);
         if (threadIdx.x == 0) {
-            double* dst = cx.resid + ((size_t)blockIdx.x * cx.Kp + j) * 5;
+            double* dst = cx.resid + ((size_t)rt * cx.Kp + j) * 5;
             for (int k = 0; k < 5; ++k) dst[k] = out[k];
         }
     }
 }
 
 // Per-column stop test and bookkeeping; the last kernel of every iteration.
-__global__ void k_finalize(IterCtx cx) {
+// One block per column sums that column's residual partials (fixed order,
+// deterministic); the last block to finish (ticket) updates the control
+// block.
+__global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
     Control* c = cx.ctrl;
     if (c->n_active == 0) return;
-    if (c->err) {           // a device error stops every column
-        for (int j = threadIdx.x; j < cx.Kp; j += blockDim.x) cx.active[j] = 0;
-        __syncthreads();
-        if (threadIdx.x == 0) c->n_active = 0;
-        return;
+    const int j = blockIdx.x, it = c->iter + 1;
+    const bool err = c->err != 0;
+    const bool check = (cx.tol > 0.f && it % cx.check_every == 0) || it >= c->max_iter;
+    const bool test = cx.tol > 0.f && it % cx.check_every == 0;
+    __shared__ double red[5][4];
+    if (err) {
+        if (threadIdx.x == 0) cx.active[j] = 0;
+    } else if (cx.active[j]) {
+        bool stop = it >= c->max_iter;
+        if (check) {
+            const int nb = cx.n_resid_n + cx.n_resid_m;
+            double s5[5] = {0, 0, 0, 0, 0};
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) s5[k] += cx.resid[((size_t)b * cx.Kp + j) * 5 + k];
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                double v = s5[k];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[k][w] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t5[5];
+                for (int k = 0; k < 5; ++k) t5[k] = red[k][0] + red[k][1] + red[k][2] + red[k][3];
+                const double sq = sqrt((double)(cx.n + cx.m_rows));
+                const double rho = cx.rho[j];
+                const double rn = sqrt(t5[0]), xn = sqrt(t5[1]), zn = sqrt(t5[2]);
+                const double sn = rho * sqrt(t5[3]), yn = rho * sqrt(t5[4]);
+                const double xz = fmax(xn, zn);
+                cx.stats[j] = rn / fmax(xz, 1e-300);
+                cx.stats[cx.Kp + j] = sn / fmax(yn, 1e-300);
+                if (test && rn <= cx.eps_abs * sq + cx.tol * xz && sn <= cx.eps_abs * sq + cx.tol * yn) {
+                    stop = true;
+                    cx.active[cx.Kp + j] = 1;   // converged
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            cx.iters[j] = it;
+            if (stop) cx.active[j] = 0;
+        }
     }
-    int it = c->iter + 1;
-    bool check = (cx.tol > 0.f && it % cx.check_every == 0) || it >= c->max_iter;
-    bool test = cx.tol > 0.f && it % cx.check_every == 0;
+    // last block: count the active columns, advance the iteration counter
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&c->ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    int nb = cx.n_resid_n + cx.n_resid_m;
-    double sq = sqrt((double)(cx.n + cx.m_rows));
-    for (int j = threadIdx.x; j < cx.Kp; j += blockDim.x) {
-        int* act = cx.active;
-        if (!act[j]) continue;
-        cx.iters[j] = it;
-        bool stop = it >= c->max_iter;
-        if (check) {
-            double s5[5] = {0, 0, 0, 0, 0};
-            for (int b = 0; b < nb; ++b)
-                for (int k = 0; k < 5; ++k) s5[k] += cx.resid[((size_t)b * cx.Kp + j) * 5 + k];
-            double rho = cx.rho[j];
-            double rn = sqrt(s5[0]), xn = sqrt(s5[1]), zn = sqrt(s5[2]);
-            double sn = rho * sqrt(s5[3]), yn = rho * sqrt(s5[4]);
-            double xz = fmax(xn, zn);
-            cx.stats[j] = rn / fmax(xz, 1e-300);
-            cx.stats[cx.Kp + j] = sn / fmax(yn, 1e-300);
-            if (test && rn <= cx.eps_abs * sq + cx.tol * xz && sn <= cx.eps_abs * sq + cx.tol * yn) {
-                stop = true;
-                act[cx.Kp + j] = 1;   // converged
-            }
-        }
-        if (stop) act[j] = 0;
-        else atomicAdd(&cnt, 1);
-    }
+    int mine = 0;
+    for (int k = threadIdx.x; k < cx.Kp; k += blockDim.x) mine += ((volatile int*)cx.active)[k] != 0;
+    atomicAdd(&cnt, mine);
     __syncthreads();
     if (threadIdx.x == 0) {
         c->n_active = cnt;
         c->iter = it;
+        c->ticket = 0;
+        __threadfence();
     }
 }
 
@@ -346,8 +380,8 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 1);
-    dim3 gm((cs.m_pad + 255) / 256, r.Kp);
-    k_reduce_rhs<false><<<gm, 256, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
+    dim3 gm(cs.m_pad / 128, r.Kp);
+    k_reduce_rhs<false><<<gm, 128, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     // solve: part = rhs . G^T (G symmetric)
@@ -359,7 +393,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 3);
-    k_reduce_solve<false><<<gm, 256, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
+    k_reduce_solve<false><<<gm, 128, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     // GEMM2: W[Kp][n_pad] = V[Kp][m_pad] . A[m_pad][n_pad]
@@ -371,41 +405,39 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 5);
-    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
-    k_q1_update<false><<<gn, 256, 0, st>>>(cx, plain_src(r.W.as<float>(), cs.n_pad), r.R1.p);
+    dim3 gn(cs.n_pad / 128, r.Kp);
+    k_q1_update<false><<<gn, 128, 0, st>>>(cx, plain_src(r.W.as<float>(), cs.n_pad), r.R1.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 6);
-    k_finalize<<<1, 1024, 0, st>>>(cx);
+    k_finalize<<<r.Kp, 128, 0, st>>>(cx);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 7);
     return LGK_OK;
 }
 
+// BF16 forms: GEMM1 and the solve leave stream-K partial sums that a reduce
+// kernel adds (rhs, q2 steps); GEMM2 runs the q1 step in its own epilogue.
 static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
     int rc;
+    dim3 gm(cs.m_pad / 128, r.Kp);
     prof_mark(r, itx, 0);
     if ((rc = tc_gemm1(r))) return rc;
     prof_mark(r, itx, 1);
-    dim3 gm((cs.m_pad + 255) / 256, r.Kp);
-    k_reduce_rhs<true><<<gm, 256, 0, st>>>(cx, plan_src(r, r.plan1), r.rhs.p);
+    k_reduce_rhs<true><<<gm, 128, 0, st>>>(cx, plan_src(r, r.plan1), r.rhs.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     if ((rc = tc_solve(r))) return rc;
     prof_mark(r, itx, 3);
-    k_reduce_solve<true><<<gm, 256, 0, st>>>(cx, plan_src(r, r.plan_s), r.V.p);
+    k_reduce_solve<true><<<gm, 128, 0, st>>>(cx, plan_src(r, r.plan_s), r.V.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     if ((rc = tc_gemm2(r))) return rc;
     prof_mark(r, itx, 5);
-    dim3 gn((cs.n_pad + 255) / 256, r.Kp);
-    k_q1_update<true><<<gn, 256, 0, st>>>(cx, plan_src(r, r.plan2), r.R1.p);
+    k_finalize<<<r.Kp, 128, 0, st>>>(cx);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 6);
-    k_finalize<<<1, 1024, 0, st>>>(cx);
-    LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 7);
     return LGK_OK;
 }
 
@@ -457,14 +489,14 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
     if ((rc = r.active.alloc((size_t)2 * Kp * 4)) || (rc = r.iters.alloc((size_t)Kp * 4))) return rc;
     if ((rc = r.ctrl.alloc(sizeof(Control)))) return rc;
-    r.n_resid_n = (cs.n_pad + 255) / 256;
-    r.n_resid_m = (cs.m_pad + 255) / 256;
+    r.n_resid_n = cs.n_pad / 128;
+    r.n_resid_m = cs.m_pad / 128;
     if ((rc = r.resid.alloc((size_t)(r.n_resid_n + r.n_resid_m) * Kp * 5 * 8))) return rc;
     if ((rc = r.stats.alloc((size_t)3 * Kp * 8))) return rc;
 
     std::vector<int> act(2 * Kp, 0);
     for (int j = 0; j < K; ++j) act[j] = 1;
-    Control c0{0, K, r.max_iter, 0};
+    Control c0{0, K, r.max_iter, 0, 0};
     LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.active.p, act.data(), act.size() * 4, cudaMemcpyHostToDevice, st));
@@ -506,8 +538,16 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     // capture a CUDA graph of `per_graph` iterations, replay until done
     int per_graph = std::max(1, std::min(r.max_iter, 5 * cs.prm.check_every));
     cudaGraph_t g = nullptr;
+    // kernel classes of one iteration, in launch order
+    if (bf16)
+        r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE, LGK_K_GEMM2,
+                        LGK_K_FINALIZE};
+    else
+        r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
+                        LGK_K_GEMM2, LGK_K_Q1_UPDATE, LGK_K_FINALIZE};
+    const size_t kpi = r.prof_class.size();
     if (cs.prm.profile) {
-        r.prof_ev.assign((size_t)per_graph * (LGK_K_COUNT + 1), nullptr);
+        r.prof_ev.assign((size_t)per_graph * (kpi + 1), nullptr);
         for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
     }
     LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -531,8 +571,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.graph_iters = per_graph;
     size_t n_nodes = 0;
     {
-        // kernels per iteration (both precisions)
-        n_nodes = (size_t)per_graph * LGK_K_COUNT;
+        n_nodes = (size_t)per_graph * kpi;
     }
 
     Control* hc = nullptr;
@@ -566,12 +605,12 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         if (!r.prof_ev.empty()) {       // iterations of this replay that did work
             int worked = std::min(per_graph, hc->iter - iter_before);
             for (int it = 0; it < worked; ++it)
-                for (int k = 0; k < LGK_K_COUNT; ++k) {
+                for (size_t k = 0; k < kpi; ++k) {
                     float ms = 0.f;
-                    const size_t e0 = (size_t)it * (LGK_K_COUNT + 1) + k;
+                    const size_t e0 = (size_t)it * (kpi + 1) + k;
                     if (cudaEventElapsedTime(&ms, r.prof_ev[e0], r.prof_ev[e0 + 1]) == cudaSuccess) {
-                        r.prof_ms[k] += ms;
-                        r.prof_n[k] += 1;
+                        r.prof_ms[r.prof_class[k]] += ms;
+                        r.prof_n[r.prof_class[k]] += 1;
                     } else {
                         cudaGetLastError();      // not sticky; keep it out of later checks
                     }

@@ -62,6 +62,7 @@ struct Control {
     int n_active;    // columns still iterating
     int max_iter;
     int err;         // DeviceError
+    int ticket;      // blocks of the finalize kernel done this iteration
 };
 
 // Point-class slots of the A columns: per target k: TS=3k, TI=3k+1, R=3k+2;

@@ -69,6 +69,7 @@ struct GemmPlan {
     const int* seg = nullptr;
     const int* tile_begin = nullptr;
     const int* tile_slots = nullptr;
+    int* tile_count = nullptr;      // per tile: segments done in the running launch
 };
 
 struct ResultData {
@@ -95,7 +96,8 @@ struct ResultData {
 
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
-    std::vector<cudaEvent_t> prof_ev;        // LGK_K_COUNT + 1 per captured iteration
+    std::vector<int> prof_class;             // kernel classes of one iteration, launch order
+    std::vector<cudaEvent_t> prof_ev;        // prof_class.size() + 1 per captured iteration
     double prof_ms[LGK_K_COUNT] = {0};
     long long prof_n[LGK_K_COUNT] = {0};
     ~ResultData();

@@ -169,30 +169,169 @@ __host__ __device__ constexpr int term_b(int NT, int t) {
 
 
 struct TcArgs {
-    const int* cta_seg;   // segments of CTA c: [cta_seg[c], cta_seg[c + 1])
-    const int* seg;       // 5 ints per segment: row tile, column tile, kb begin, kb end, slot
-    int n_tile;           // columns per tile (multiple of 16, <= 256)
-    int tmem_cols;        // columns of one accumulator (power of two >= n_tile); two of them
+    const int* cta_seg;     // segments of CTA c: [cta_seg[c], cta_seg[c + 1])
+    const int* seg;         // 5 ints per segment: row tile, column tile, kb begin, kb end, slot
+    const int* tile_begin;  // slots of output tile t: tile_slots[tile_begin[t] .. tile_begin[t + 1])
+    const int* tile_slots;
+    int* tile_count;        // per output tile: segments finished this launch (reset by the last)
+    int row_tiles;
+    int n_tile;             // columns per tile (multiple of 16, <= 256)
+    int tmem_cols;          // columns of one accumulator (power of two >= n_tile)
+    int nbuf;               // accumulators in TMEM (2 or 4; nbuf * tmem_cols <= 512)
     int stages;
     int stage_bytes;
-    float* part;          // [slot][n_tile][128] segment partial sums
+    float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
+    void* out;              // EPI_RHS: rhs [3][Kp][m_pad]; EPI_SOLVE: V [2][Kp][m_pad];
+                            // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
 };
+
+// What a finished output tile becomes.  EPI_PARTIAL: every segment stores its
+// partial sum in its slot and a separate element-wise kernel adds a tile's
+// slots (GEMM1 and the solve: few output tiles, each split over ~6 CTAs, so
+// finishing them inside the GEMM would leave the summing to a handful of CTAs
+// at the end of the kernel).  Otherwise the element-wise step of the
+// iteration that consumes this GEMM's result is applied by the CTA that
+// completes the tile (GEMM2: ~2 tiles per CTA, most of them whole):
+//   EPI_RHS    rhs = A R1 + q2 - 2 P2(q2), split into three BF16 terms
+//   EPI_SOLVE  v = S^{-1} rhs: q2' = v + P2(q2), v split into two BF16 terms,
+//              residual partials of the m-block
+//   EPI_Q1     W = A^T V: q1' = P1(q1) - c/rho - W, R1' = 2 P1(q1') - q1' - c/rho
+//              as two BF16 terms, residual partials of the n-block
+enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3 };
 
 constexpr int kThreads = 192;
 constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile
 
-template <int NA, int NB, int NT, bool A_MN>
+__device__ inline void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Apply the element-wise step to 16 columns [j0, j0 + 16) of row `row`,
+// accumulating the 5 residual terms per column (block-reduced by the caller).
+// Only 4 warps per SM run this, so every input of the 16 columns is loaded
+// before anything is computed or stored: the loads are then in flight
+// together instead of one dependent round trip per column.
+template <int EPI>
+__device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j0, const float v[16],
+                              float res[16][5]) {
+    if (EPI == EPI_RHS) {
+        const size_t plane = (size_t)cx.Kp * cx.m_pad;
+        const float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
+        float q[16], wb[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            q[c] = q2p[(size_t)c * cx.m_pad];
+            wb[c] = __ldg(cx.wbot + j0 + c);
+        }
+        const bool tau_row = row >= cx.n_beams && row < cx.m;
+        const double dr = tau_row ? cx.Dr[row] : 0.0;
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
+            const float r = v[c] + q[c] - 2.f * fminf(q[c], bb);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(r);
+            const float r1 = r - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const size_t o = (size_t)c * cx.m_pad;
+            d[o] = hi;
+            d[plane + o] = mid;
+            d[2 * plane + o] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+        }
+    } else if (EPI == EPI_SOLVE) {
+        const size_t plane = (size_t)cx.Kp * cx.m_pad;
+        float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
+        float q[16], wb[16];
+        int act[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            q[c] = q2p[(size_t)c * cx.m_pad];
+            wb[c] = __ldg(cx.wbot + j0 + c);
+            act[c] = cx.active[j0 + c];
+        }
+        const bool tau_row = row >= cx.n_beams && row < cx.m;
+        const double dr = tau_row ? cx.Dr[row] : 0.0;
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
+            const float zo = fminf(q[c], bb), qn = v[c] + zo;
+            const size_t o = (size_t)c * cx.m_pad;
+            if (act[c]) q2p[o] = qn;
+            __nv_bfloat16 hi, lo;
+            split_bf16(v[c], hi, lo);
+            d[o] = hi;
+            d[plane + o] = lo;
+            const float yo = q[c] - zo, zn = fminf(qn, bb), yn = qn - zn;
+            const float r = yn - yo, x = qn - yo, s = zn - zo;
+            res[c][0] = r * r; res[c][1] = x * x; res[c][2] = zn * zn; res[c][3] = s * s; res[c][4] = yn * yn;
+        }
+    } else {
+        const size_t plane = (size_t)cx.Kp * cx.n_pad;
+        float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
+        const int sl = cx.col_slot[row];
+        const float c_p = cx.c_slot[sl];
+        float q[16], u[16], ir[16];
+        int act[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            q[c] = q1p[(size_t)c * cx.n_pad];
+            u[c] = __ldg(cx.utab + (j0 + c) * cx.n_slot + sl);
+            ir[c] = __ldg(cx.inv_rho + j0 + c);
+            act[c] = cx.active[j0 + c];
+        }
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.n_pad + row;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            Q1Update qq = q1_update(q[c], v[c], u[c], c_p * ir[c]);
+            const size_t o = (size_t)c * cx.n_pad;
+            if (act[c]) q1p[o] = qq.qn;
+            __nv_bfloat16 hi, lo;
+            split_bf16(qq.r1, hi, lo);
+            d[o] = hi;
+            d[plane + o] = lo;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) res[c][k] = qq.res[k];
+        }
+    }
+}
+
+// Block-reduce (over the 128 epilogue threads) the residual terms of 16
+// columns and store them as this tile's partial for columns j0..j0+15.
+__device__ inline void epi_resid(float res[16][5], float* red, double* dst, int lane, int ew, int et) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            float v = res[c][k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[(ew * 16 + c) * 5 + k] = v;
+        }
+    epi_bar();
+    if (et < 80) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) s += (double)red[w * 80 + et];
+        dst[et] = s;
+    }
+    epi_bar();
+}
+
+template <int NA, int NB, int NT, bool A_MN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcArgs a, Control* ctrl) {
+              TcArgs a, IterCtx cx) {
+    Control* ctrl = cx.ctrl;
     if (ctrl->n_active == 0 || ctrl->err) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = a.stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * a.stage_bytes);
     // bars: [0, S) stage full, [S, 2S) stage empty, 2S + b accumulator b full,
-    // 2S + 2 + b accumulator b drained
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 4);
+    // 2S + 4 + b accumulator b drained (b < nbuf <= 4)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 8);
+    int* sh_last = reinterpret_cast<int*>(bars + 2 * S + 8) + 1;
+    float* red = reinterpret_cast<float*>(bars + 2 * S + 9);        // [4 warps][16][5]
+    const int NBUF = a.nbuf;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
@@ -200,12 +339,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int b_bytes = a.n_tile * 128;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2 * S + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
-        mbar_init(smem_u32(&bars[2 * S + 2]), 4);     // one arrival per epilogue warp
-        mbar_init(smem_u32(&bars[2 * S + 3]), 4);
+        for (int s = 0; s < 2 * S + 4; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[2 * S + 4 + b]), 4);   // one per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 2 * a.tmem_cols);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * a.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -252,8 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int it = 0;
         for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
             const int* g = a.seg + 5 * sg;
-            const int b = u & 1;
-            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 2 + b]), (uint32_t)((u >> 1) & 1) ^ 1u, err);
+            const int b = u % NBUF;
+            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 4 + b]), (uint32_t)((u / NBUF) & 1) ^ 1u, err);
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(b * a.tmem_cols);
             for (int kb = g[2]; kb < g[3]; ++kb, ++it) {
@@ -282,32 +420,89 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_commit(smem_u32(&bars[2 * S + b]));      // accumulator b complete
         }
     } else if (warp >= 2) {
-        // ---------------- epilogue: accumulator -> segment slot
+        // ---------------- epilogue
         const int ew = warp & 3;                        // TMEM lane quarter of this warp
+        const int et = threadIdx.x - 64;                // 0..127
         const int r = ew * 32 + lane;                   // row within the tile
+        const bool check = EPI != EPI_RHS && is_check_iter(ctrl, cx.check_every, cx.tol);
         bool ok = true;
         for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
-            const int b = u & 1;
-            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u >> 1) & 1), err);
+            const int b = u % NBUF;
+            const int* g = a.seg + 5 * sg;
+            const int rt = g[0], ct = g[1], slot = g[4];
+            const int tile = ct * a.row_tiles + rt;
+            const int sb = a.tile_begin[tile], se = a.tile_begin[tile + 1];
+            const int row = rt * 128 + r, col0 = ct * a.n_tile;
+            double* rdst = cx.resid + ((size_t)((EPI == EPI_SOLVE ? cx.n_resid_n : 0) + rt) * cx.Kp + col0) * 5;
+            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
             tc_fence_after();
-            float* out = a.part + (size_t)a.seg[5 * sg + 4] * a.n_tile * 128 + r;
             const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(b * a.tmem_cols);
-            for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                float v[16];
-                tmem_ld16(base + (uint32_t)c0, v);
+            if (EPI == EPI_PARTIAL) {
+                float* own = a.part + (size_t)slot * a.n_tile * 128 + r;
+                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)c0, v);
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) out[(size_t)(c0 + jj) * 128] = ok ? v[jj] : 0.f;
+                    for (int c = 0; c < 16; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
+            } else if (se - sb == 1) {
+                // the whole k range of the tile is in this accumulator
+                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
+                    float v[16], res[16][5];
+                    tmem_ld16(base + (uint32_t)c0, v);
+                    if (!ok)
+                        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+                    epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, et);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
+            } else {
+                // partial: store it; the CTA completing the tile sums the
+                // tile's slots in k order and applies the step
+                float* own = a.part + (size_t)slot * a.n_tile * 128 + r;
+                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(base + (uint32_t)c0, v);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
+                __threadfence();
+                epi_bar();
+                if (et == 0) *sh_last = atomicAdd(&a.tile_count[tile], 1) == se - sb - 1;
+                epi_bar();
+                if (*sh_last) {
+                    __threadfence();
+                    for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
+                        float v[16], res[16][5];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) v[c] = 0.f;
+                        for (int k = sb; k < se; ++k) {
+                            const float* ps = a.part + (size_t)a.tile_slots[k] * a.n_tile * 128 + r;
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
+                        }
+                        epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                        if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, et);
+                    }
+                    if (et == 0) a.tile_count[tile] = 0;
+                }
+                epi_bar();
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 2 + b]));
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * a.tmem_cols);
+        tmem_dealloc(tmem, NBUF * a.tmem_cols);
     }
 }
 
@@ -354,7 +549,7 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
 
 static constexpr int kSmemLimit = 232448;    // 227 KB opt-in per block
 
-static int smem_extra() { return 1024 + 8 * (2 * 8 + 4) + 16; }
+static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 16 + 4 * 16 * 5 * 4; }
 
 int sm_count() {
     static int n = 0;
@@ -390,13 +585,19 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile) {
         }
     }
     cta_seg[grid] = nseg;
+    // number the slots tile by tile, in k order, so a tile's partial sums are
+    // contiguous: slot = tile_begin[t] + position of the segment in the tile
     std::vector<int> tile_slots;
     for (size_t t = 0; t < per_tile.size(); ++t) {
         tile_begin[t] = (int)tile_slots.size();
-        tile_slots.insert(tile_slots.end(), per_tile[t].begin(), per_tile[t].end());
+        for (int sid : per_tile[t]) {
+            seg[5 * sid + 4] = (int)tile_slots.size();
+            tile_slots.push_back((int)tile_slots.size());
+        }
     }
     tile_begin[per_tile.size()] = (int)tile_slots.size();
     std::vector<int> all;
+    all.insert(all.end(), rows * col_tiles, 0);          // tile_count, zero between launches
     all.insert(all.end(), cta_seg.begin(), cta_seg.end());
     all.insert(all.end(), seg.begin(), seg.end());
     all.insert(all.end(), tile_begin.begin(), tile_begin.end());
@@ -404,7 +605,9 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile) {
     int rc;
     if ((rc = P.buf.alloc(all.size() * 4))) return rc;
     LGK_CUDA_TRY(cudaMemcpy(P.buf.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
-    const int* d = P.buf.as<int>();
+    int* d0 = P.buf.as<int>();
+    P.tile_count = d0;
+    const int* d = d0 + rows * col_tiles;
     P.grid = grid;
     P.nseg = nseg;
     P.rows = rows;
@@ -417,14 +620,19 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile) {
     return LGK_OK;
 }
 
-template <int NA, int NB, int NT, bool A_MN>
-static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, float* part,
-                  Control* ctrl, cudaStream_t st) {
+template <int NA, int NB, int NT, bool A_MN, int EPI>
+static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
+                  void* out) {
     TcArgs a{};
     a.cta_seg = P.cta_seg;
     a.seg = P.seg;
+    a.tile_begin = P.tile_begin;
+    a.tile_slots = P.tile_slots;
+    a.tile_count = P.tile_count;
+    a.row_tiles = P.rows;
     a.n_tile = P.n_tile;
-    a.part = part;
+    a.part = r.part.as<float>();
+    a.out = out;
     a.stage_bytes = NA * kABytes + NB * a.n_tile * 128;
     a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
     if (a.stages < 2) {
@@ -433,8 +641,9 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     }
     a.tmem_cols = 32;
     while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
+    a.nbuf = 4 * a.tmem_cols <= 512 ? 4 : 2;
     size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
-    k_tc_gemm<NA, NB, NT, A_MN><<<P.grid, kThreads, smem, st>>>(mA, mB, a, ctrl);
+    k_tc_gemm<NA, NB, NT, A_MN, EPI><<<P.grid, kThreads, smem, r.cs->stream>>>(mA, mB, a, make_ctx_public(r));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -451,9 +660,9 @@ static int maps_for(ResultData& r, TcMaps& M) {
     return LGK_OK;
 }
 
-template <int NA, int NB, int NT, bool A_MN>
+template <int NA, int NB, int NT, bool A_MN, int EPI>
 static int set_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -466,11 +675,11 @@ static int set_smem_attr() {
 int tc_prepare(ResultData& r) {
     CaseData& cs = *r.cs;
     int rc;
-    if ((rc = set_smem_attr<1, 2, 2, false>())) return rc;
-    if ((rc = set_smem_attr<2, 2, 3, false>())) return rc;
-    if ((rc = set_smem_attr<3, 3, 6, false>())) return rc;
-    if ((rc = set_smem_attr<1, 2, 2, true>())) return rc;
-    if ((rc = set_smem_attr<2, 2, 3, true>())) return rc;
+    if ((rc = set_smem_attr<1, 2, 2, false, EPI_PARTIAL>())) return rc;
+    if ((rc = set_smem_attr<2, 2, 3, false, EPI_PARTIAL>())) return rc;
+    if ((rc = set_smem_attr<3, 3, 6, false, EPI_PARTIAL>())) return rc;
+    if ((rc = set_smem_attr<1, 2, 2, true, EPI_Q1>())) return rc;
+    if ((rc = set_smem_attr<2, 2, 3, true, EPI_Q1>())) return rc;
     if ((rc = maps_for(r, r.maps))) return rc;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
     if ((rc = build_plan(r.plan1, mt, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile))) return rc;
@@ -482,22 +691,17 @@ int tc_prepare(ResultData& r) {
 }
 
 int tc_gemm1(ResultData& r) {
-    CaseData& cs = *r.cs;
-    if (cs.na == 2)
-        return launch<2, 2, 3, false>(r.maps.A_k, r.maps.R1, r.plan1, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
-    return launch<1, 2, 2, false>(r.maps.A_k, r.maps.R1, r.plan1, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
+    if (r.cs->na == 2) return launch<2, 2, 3, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr);
+    return launch<1, 2, 2, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr);
 }
 
 int tc_solve(ResultData& r) {
-    CaseData& cs = *r.cs;
-    return launch<3, 3, 6, false>(r.maps.G3, r.maps.rhs, r.plan_s, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
+    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr);
 }
 
 int tc_gemm2(ResultData& r) {
-    CaseData& cs = *r.cs;
-    if (cs.na == 2)
-        return launch<2, 2, 3, true>(r.maps.A_mn, r.maps.V, r.plan2, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
-    return launch<1, 2, 2, true>(r.maps.A_mn, r.maps.V, r.plan2, r.part.as<float>(), r.ctrl.as<Control>(), cs.stream);
+    if (r.cs->na == 2) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p);
+    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p);
 }
 
 }  // namespace lgk
