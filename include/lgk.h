@@ -230,6 +230,54 @@ enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLV
  * pointer may be NULL.  LGK_EINVAL if the solve was not profiled. */
 int lgk_fetch_profile(const lgk_result* res, double* ms, long long* launches);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop for planning requests (a case plus its K weightings) that
+ * arrive over time.  Each admitted request runs lgk_create_case,
+ * lgk_solve_weightings and lgk_fetch_times on a worker thread with its own
+ * CUDA stream, so requests that arrive while others are on the GPU run
+ * alongside them.  Admission is first come, first served under a device-
+ * memory budget: a request starts once its estimated peak footprint (set-up
+ * temporaries included) fits next to the requests in flight; one that can
+ * never fit fails with LGK_EBUDGET.  A request's results do not depend on
+ * what runs beside it (bitwise: every reduction has a fixed order).
+ * (The paper plans one case at a time; this is the serving form of the
+ * library, not a step of the method.)
+ */
+typedef struct lgk_server lgk_server;
+
+typedef struct {
+    lgk_params case_params;  /* per-case parameters (its stream field is ignored)           */
+    size_t hbm_budget;       /* bytes for the requests in flight; 0 = 90 % of free memory   */
+    int workers;             /* requests in flight at most (>= 1)                           */
+    double tol;              /* stop tolerance of every solve (lgk_solve_weightings)        */
+    int max_iter;
+    double w0_bot;           /* rho rule: rho = rho0_per_beta * beta * sqrt(w0_bot / w_BOT) */
+    double rho0_per_beta;
+} lgk_server_params;
+
+typedef struct {
+    int status;              /* lgk_status of the request                                   */
+    int K, n_iso;
+    double queue_ms;         /* submit -> admitted                                           */
+    double setup_ms;         /* lgk_create_case                                              */
+    double solve_ms;         /* lgk_solve_weightings + lgk_fetch_times                       */
+    double total_ms;         /* submit -> done                                               */
+    int max_iters;           /* iterations of the slowest weighting                          */
+    int converged;           /* weightings that met the tolerance                            */
+    size_t footprint;        /* estimated peak device bytes used for admission               */
+} lgk_request_info;
+
+int lgk_server_create(const lgk_server_params* p, lgk_server** out);
+/* Copies the case arrays and W (K x 4); *id receives the request id. */
+int lgk_server_submit(lgk_server* s, const lgk_case_desc* desc, int K, const double* W,
+                      long long* id);
+/* Waits (at most timeout_ms) for request id; fills *info and, if not NULL,
+ * t (K x 24N) and tau (K x N).  A request can be waited for once. */
+int lgk_server_wait(lgk_server* s, long long id, int timeout_ms, lgk_request_info* info,
+                    double* t, double* tau);
+/* Finishes the requests in flight, drops queued ones, joins the workers. */
+void lgk_server_destroy(lgk_server* s);
+
 void lgk_free_result(lgk_result* res);
 void lgk_destroy_case(lgk_case* cs);
 const char* lgk_last_error(void);

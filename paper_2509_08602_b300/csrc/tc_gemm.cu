@@ -135,6 +135,17 @@ __device__ inline void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Shared-memory matrix descriptor (tcgen05 format): start, leading and stride
 // byte offsets in 16-byte units, descriptor version 1, 128-byte swizzle.
 __device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -199,25 +210,27 @@ struct TcArgs {
 //              as two BF16 terms, residual partials of the n-block
 enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3 };
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;               // 2 producer/MMA warps + 8 epilogue warps
+constexpr int kEpiThreads = 256;
+constexpr int kChunk = 8;                   // columns per epilogue step
 constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile
 
-__device__ inline void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ inline void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// Apply the element-wise step to 16 columns [j0, j0 + 16) of row `row`,
+// Apply the element-wise step to kChunk columns [j0, j0 + kChunk) of row `row`,
 // accumulating the 5 residual terms per column (block-reduced by the caller).
-// Only 4 warps per SM run this, so every input of the 16 columns is loaded
+// Only 8 warps per SM run this, so every input of the chunk's columns is loaded
 // before anything is computed or stored: the loads are then in flight
 // together instead of one dependent round trip per column.
 template <int EPI>
-__device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j0, const float v[16],
-                              float res[16][5]) {
+__device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j0, const float v[kChunk],
+                              float res[kChunk][5]) {
     if (EPI == EPI_RHS) {
         const size_t plane = (size_t)cx.Kp * cx.m_pad;
         const float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
-        float q[16], wb[16];
+        float q[kChunk], wb[kChunk];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             q[c] = q2p[(size_t)c * cx.m_pad];
             wb[c] = __ldg(cx.wbot + j0 + c);
         }
@@ -225,7 +238,7 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         const double dr = tau_row ? cx.Dr[row] : 0.0;
         __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
             const float r = v[c] + q[c] - 2.f * fminf(q[c], bb);
             const __nv_bfloat16 hi = __float2bfloat16_rn(r);
@@ -239,10 +252,10 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
     } else if (EPI == EPI_SOLVE) {
         const size_t plane = (size_t)cx.Kp * cx.m_pad;
         float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
-        float q[16], wb[16];
-        int act[16];
+        float q[kChunk], wb[kChunk];
+        int act[kChunk];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             q[c] = q2p[(size_t)c * cx.m_pad];
             wb[c] = __ldg(cx.wbot + j0 + c);
             act[c] = cx.active[j0 + c];
@@ -251,7 +264,7 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         const double dr = tau_row ? cx.Dr[row] : 0.0;
         __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
             const float zo = fminf(q[c], bb), qn = v[c] + zo;
             const size_t o = (size_t)c * cx.m_pad;
@@ -269,10 +282,10 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
         const int sl = cx.col_slot[row];
         const float c_p = cx.c_slot[sl];
-        float q[16], u[16], ir[16];
-        int act[16];
+        float q[kChunk], u[kChunk], ir[kChunk];
+        int act[kChunk];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             q[c] = q1p[(size_t)c * cx.n_pad];
             u[c] = __ldg(cx.utab + (j0 + c) * cx.n_slot + sl);
             ir[c] = __ldg(cx.inv_rho + j0 + c);
@@ -280,7 +293,7 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         }
         __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.n_pad + row;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
+        for (int c = 0; c < kChunk; ++c) {
             Q1Update qq = q1_update(q[c], v[c], u[c], c_p * ir[c]);
             const size_t o = (size_t)c * cx.n_pad;
             if (act[c]) q1p[o] = qq.qn;
@@ -294,24 +307,27 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
     }
 }
 
-// Block-reduce (over the 128 epilogue threads) the residual terms of 16
-// columns and store them as this tile's partial for columns j0..j0+15.
-__device__ inline void epi_resid(float res[16][5], float* red, double* dst, int lane, int ew, int et) {
+// Reduce the residual terms of kChunk columns over the 128 rows (the 4 warps
+// of one column half `hf`) and store them as this tile's partial for those
+// columns.  Both halves call it the same number of times (barriers).
+__device__ inline void epi_resid(float res[kChunk][5], float* red, double* dst, int lane, int ew, int hf,
+                                 int et) {
 #pragma unroll
-    for (int c = 0; c < 16; ++c)
+    for (int c = 0; c < kChunk; ++c)
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             float v = res[c][k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[(ew * 16 + c) * 5 + k] = v;
+            if (lane == 0) red[((hf * 4 + ew) * kChunk + c) * 5 + k] = v;
         }
     epi_bar();
-    if (et < 80) {
+    const int e = et & 127;
+    if (e < kChunk * 5) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) s += (double)red[w * 80 + et];
-        dst[et] = s;
+        for (int w = 0; w < 4; ++w) s += (double)red[(hf * 4 + w) * kChunk * 5 + e];
+        dst[e] = s;
     }
     epi_bar();
 }
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // 2S + 4 + b accumulator b drained (b < nbuf <= 4)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 8);
     int* sh_last = reinterpret_cast<int*>(bars + 2 * S + 8) + 1;
-    float* red = reinterpret_cast<float*>(bars + 2 * S + 9);        // [4 warps][16][5]
+    float* red = reinterpret_cast<float*>(bars + 2 * S + 9);        // [8 warps][kChunk][5]
     const int NBUF = a.nbuf;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -340,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2 * S + 4; ++s) mbar_init(smem_u32(&bars[s]), 1);
-        for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[2 * S + 4 + b]), 4);   // one per epilogue warp
+        for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[2 * S + 4 + b]), 8);   // one per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * a.tmem_cols);
@@ -420,11 +436,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_commit(smem_u32(&bars[2 * S + b]));      // accumulator b complete
         }
     } else if (warp >= 2) {
-        // ---------------- epilogue
+        // ---------------- epilogue (8 warps)
         const int ew = warp & 3;                        // TMEM lane quarter of this warp
-        const int et = threadIdx.x - 64;                // 0..127
+        const int hf = (warp - 2) >> 2;                 // column half
+        const int et = threadIdx.x - 64;                // 0..255
         const int r = ew * 32 + lane;                   // row within the tile
-        const bool check = EPI != EPI_RHS && is_check_iter(ctrl, cx.check_every, cx.tol);
+        const int half = a.n_tile / 2;                  // multiple of kChunk
+        const int cbeg = hf * half, cend = cbeg + half;
+        const bool check = EPI != EPI_PARTIAL && EPI != EPI_RHS && is_check_iter(ctrl, cx.check_every, cx.tol);
         bool ok = true;
         for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
             const int b = u % NBUF;
@@ -437,64 +456,55 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
             tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(b * a.tmem_cols);
-            if (EPI == EPI_PARTIAL) {
+            if (EPI == EPI_PARTIAL || se - sb > 1) {
+                // store this segment's partial sum in its slot
                 float* own = a.part + (size_t)slot * a.n_tile * 128 + r;
-                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(base + (uint32_t)c0, v);
+                for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                    float v[kChunk];
+                    tmem_ld8(base + (uint32_t)c0, v);
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
+                    for (int c = 0; c < kChunk; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
-            } else if (se - sb == 1) {
-                // the whole k range of the tile is in this accumulator
-                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                    float v[16], res[16][5];
-                    tmem_ld16(base + (uint32_t)c0, v);
-                    if (!ok)
-                        for (int c = 0; c < 16; ++c) v[c] = 0.f;
-                    epi_op<EPI>(cx, a, row, col0 + c0, v, res);
-                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, et);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
-            } else {
-                // partial: store it; the CTA completing the tile sums the
-                // tile's slots in k order and applies the step
-                float* own = a.part + (size_t)slot * a.n_tile * 128 + r;
-                for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(base + (uint32_t)c0, v);
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
-                __threadfence();
-                epi_bar();
-                if (et == 0) *sh_last = atomicAdd(&a.tile_count[tile], 1) == se - sb - 1;
-                epi_bar();
-                if (*sh_last) {
+                if (EPI != EPI_PARTIAL) {
+                    // the CTA completing the tile sums its slots in k order
                     __threadfence();
-                    for (int c0 = 0; c0 < a.n_tile; c0 += 16) {
-                        float v[16], res[16][5];
+                    epi_bar();
+                    if (et == 0) *sh_last = atomicAdd(&a.tile_count[tile], 1) == se - sb - 1;
+                    epi_bar();
+                    if (*sh_last) {
+                        __threadfence();
+                        for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                            float v[kChunk], res[kChunk][5];
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) v[c] = 0.f;
-                        for (int k = sb; k < se; ++k) {
-                            const float* ps = a.part + (size_t)a.tile_slots[k] * a.n_tile * 128 + r;
+                            for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
+                            for (int k = sb; k < se; ++k) {
+                                const float* ps = a.part + (size_t)a.tile_slots[k] * a.n_tile * 128 + r;
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
+                                for (int c = 0; c < kChunk; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
+                            }
+                            epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                            if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
                         }
-                        epi_op<EPI>(cx, a, row, col0 + c0, v, res);
-                        if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, et);
+                        if (et == 0) a.tile_count[tile] = 0;
                     }
-                    if (et == 0) a.tile_count[tile] = 0;
+                    epi_bar();
                 }
-                epi_bar();
+            } else {
+                // the whole k range of the tile is in this accumulator
+                for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                    float v[kChunk], res[kChunk][5];
+                    tmem_ld8(base + (uint32_t)c0, v);
+                    if (!ok)
+                        for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
+                    epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
             }
         }
     }
@@ -509,15 +519,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ------------------------------------------------------------- host side
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // thread-safe one-time lookup (the serving workers create maps concurrently)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -549,15 +560,15 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
 
 static constexpr int kSmemLimit = 232448;    // 227 KB opt-in per block
 
-static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 16 + 4 * 16 * 5 * 4; }
+static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 16 + 8 * kChunk * 5 * 4; }
 
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-    }
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+        return v;
+    }();
     return n;
 }
 

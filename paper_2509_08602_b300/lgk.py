@@ -46,6 +46,18 @@ class Params(C.Structure):
                 ("profile", C.c_int)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("case_params", Params), ("hbm_budget", C.c_size_t), ("workers", C.c_int),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("w0_bot", C.c_double),
+                ("rho0_per_beta", C.c_double)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("K", C.c_int), ("n_iso", C.c_int), ("queue_ms", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("total_ms", C.c_double),
+                ("max_iters", C.c_int), ("converged", C.c_int), ("footprint", C.c_size_t)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_2509_08602_b300.build`")
@@ -67,6 +79,14 @@ def _load():
     lib.lgk_fetch_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_longlong)]
     lib.lgk_fetch_doses_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     lib.lgk_fetch_doses_device.restype = C.c_int
+    lib.lgk_server_create.argtypes = [P(ServerParams), P(C.c_void_p)]
+    lib.lgk_server_submit.argtypes = [C.c_void_p, P(CaseDesc), C.c_int, P(C.c_double),
+                                      P(C.c_longlong)]
+    lib.lgk_server_wait.argtypes = [C.c_void_p, C.c_longlong, C.c_int, P(RequestInfo),
+                                    P(C.c_double), P(C.c_double)]
+    lib.lgk_server_destroy.argtypes = [C.c_void_p]
+    for f in ("lgk_server_create", "lgk_server_submit", "lgk_server_wait"):
+        getattr(lib, f).restype = C.c_int
     lib.lgk_free_result.argtypes = [C.c_void_p]
     lib.lgk_destroy_case.argtypes = [C.c_void_p]
     lib.lgk_last_error.restype = C.c_char_p
@@ -132,6 +152,27 @@ class Result:
 
     def __del__(self):
         self.close()
+
+
+def _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal, d_oar):
+    """CaseDesc over contiguous copies; returns (desc, arrays to keep alive)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    struct_id = np.ascontiguousarray(struct_id, dtype=np.uint16)
+    d_presc = np.ascontiguousarray(np.atleast_1d(d_presc), dtype=np.float64)
+    q_area = np.ascontiguousarray(np.atleast_1d(q_area), dtype=np.float64)
+    q_vol = np.ascontiguousarray(np.atleast_1d(q_vol), dtype=np.float64)
+    d_oar = None if d_oar is None or len(d_oar) == 0 else np.ascontiguousarray(d_oar, dtype=np.float64)
+    if phi.shape[1] != 24 * int(n_iso) or kind.shape[0] != phi.shape[0] or struct_id.shape[0] != phi.shape[0]:
+        raise LgkError(1, "phi must be n_pts x 24 n_iso; kind and struct_id of length n_pts")
+    d = CaseDesc(n_iso=int(n_iso), n_pts=int(phi.shape[0]), n_targets=int(d_presc.shape[0]),
+                 n_oars=0 if d_oar is None else int(d_oar.shape[0]),
+                 phi=_ptr(phi, C.c_double), kind=_ptr(kind, C.c_uint8),
+                 struct_id=_ptr(struct_id, C.c_uint16), d_presc=_ptr(d_presc, C.c_double),
+                 q_area=_ptr(q_area, C.c_double), q_vol=_ptr(q_vol, C.c_double),
+                 d_oar=_ptr(d_oar, C.c_double), d_ld1=float(d_ld1), d_ld2=float(d_ld2),
+                 phi_cal=float(phi_cal))
+    return d, (phi, kind, struct_id, d_presc, q_area, q_vol, d_oar)
 
 
 def create_case(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal,
@@ -243,6 +284,52 @@ def fetch_profile(res: Result) -> dict:
     n = np.zeros(len(KERNELS), np.int64)
     _check(_lib.lgk_fetch_profile(res._h, _ptr(ms, C.c_double), _ptr(n, C.c_longlong)))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+class Server:
+    """Serving loop (lgk_server): requests admitted first come, first served
+    under a device-memory budget, run on worker threads with their own
+    streams."""
+
+    def __init__(self, *, workers=2, hbm_budget=0, tol=1e-4, max_iter=20000, w0_bot=1e-4,
+                 rho0_per_beta=1.1e3, params: Params | None = None):
+        sp = ServerParams(case_params=params if params is not None else default_params(),
+                          hbm_budget=int(hbm_budget), workers=int(workers), tol=float(tol),
+                          max_iter=int(max_iter), w0_bot=float(w0_bot),
+                          rho0_per_beta=float(rho0_per_beta))
+        self._h = C.c_void_p()
+        _check(_lib.lgk_server_create(C.byref(sp), C.byref(self._h)))
+
+    def submit(self, phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal,
+               W, d_oar=None) -> int:
+        d, keep = _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2,
+                        phi_cal, d_oar)
+        W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+        rid = C.c_longlong()
+        _check(_lib.lgk_server_submit(self._h, C.byref(d), int(W.shape[0]), _ptr(W, C.c_double),
+                                      C.byref(rid)))
+        del keep                     # the library copied everything
+        return rid.value
+
+    def wait(self, rid: int, n_iso: int, K: int, timeout_ms: int = 600000):
+        """(info dict, t (K x 24N), tau (K x N)) of request rid."""
+        info = RequestInfo()
+        t = np.zeros((K, 24 * n_iso))
+        tau = np.zeros((K, n_iso))
+        rc = _lib.lgk_server_wait(self._h, int(rid), int(timeout_ms), C.byref(info),
+                                  _ptr(t, C.c_double), _ptr(tau, C.c_double))
+        out = {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+        if rc != 0:
+            raise LgkError(rc, _lib.lgk_last_error().decode(errors="replace"))
+        return out, t, tau
+
+    def close(self):
+        if self._h:
+            _lib.lgk_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def launch_count() -> int:
