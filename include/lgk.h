@@ -194,6 +194,24 @@ int lgk_fetch_doses(const lgk_result* res, const double* phi_eval, int n_eval, d
 int lgk_fetch_doses_device(const lgk_result* res, const double* phi_eval_dev, int n_eval,
                            double* dose_dev);
 
+/*
+ * lgk_fetch_metrics -- clinical metrics of every plan, on the device.
+ *
+ * Definitions of Sec. 2.A with the conventions of Sec. 3.B, evaluated on
+ * caller points (e.g. a regular grid) from the doses d = phi_eval t:
+ *   coverage    = |target AND d >= D_k| / |target|      (D_k: the point's target)
+ *   selectivity = |target AND d >= D_k| / |d >= min_k D_k|
+ *   gi          = |d >= D/2| / |d >= D|  (NaN unless all prescriptions are equal)
+ *   bot         = sum over isocenters of the longest sector time (its collimator
+ *                 times summed), minutes
+ * phi_eval: n_eval x 24N (host); label: n_eval target index per point, -1
+ * outside every target (host).  Outputs: K values each (host; any may be
+ * NULL).  Counts are exact integers on the device (FP64 doses), so the
+ * metrics do not depend on the evaluation order.
+ */
+int lgk_fetch_metrics(const lgk_result* res, const double* phi_eval, int n_eval, const int* label,
+                      double* coverage, double* selectivity, double* gi, double* bot);
+
 /* Per-column statistics (each pointer may be NULL; arrays of K):
  * iterations run, dual objective c^T z1 (FP64 on the device), relative primal
  * and dual residuals at the last test, converged flag. */
@@ -211,6 +229,106 @@ int lgk_fetch_stats(const lgk_result* res, int* iters, double* obj, double* rel_
 int lgk_solve_weightings_warm(lgk_case* cs, int K, const double* W, const double* rho,
                               double w0_bot, double rho0, double tol, int max_iter,
                               const double* q1_init, const double* q2_init, lgk_result** out);
+
+/*
+ * lgk_solve_weightings_masked -- as lgk_solve_weightings_warm, with a
+ * selection of dose points per weighting (Sec. 2.C: the second pass samples
+ * its low-dose points per weighting from the union of all weightings'
+ * low-dose volumes, and a weighting's LP leaves out the union points not
+ * sampled for it by zeroing their upper bounds u).
+ *   mask: n_pts x ceil(K/32) uint32 host array; point p belongs to weighting j
+ *         when bit (j % 32) of mask[p * ceil(K/32) + j / 32] is set.  NULL:
+ *         every point in every weighting.  Bits past K are ignored.
+ * A point left out of weighting j gets u = 0 there (so its x is 0 and the
+ * weighting solves the LP of its selected points only), and the point counts
+ * N_alpha that normalise u (Appendix A) are weighting j's selected counts; a
+ * class with no selected point drops out of that weighting's objective.
+ * q1_init, q2_init: as in lgk_solve_weightings_warm (NULL: zero state).
+ */
+int lgk_solve_weightings_masked(lgk_case* cs, int K, const double* W, const double* rho,
+                                double w0_bot, double rho0, double tol, int max_iter,
+                                const uint32_t* mask, const double* q1_init, const double* q2_init,
+                                lgk_result** out);
+
+/* ------------------------------------------------------------------------
+ * Two-pass optimisation (Sec. 2.C).  The first pass takes its low-dose
+ * points from a geometric expansion of the targets; the second takes them,
+ * per weighting, from the low-dose volume of that weighting's first-pass
+ * plan: the candidate points whose dose lies in [D_LD, D_LD + Delta).  The
+ * weightings' volumes differ, so their points are sampled with Algorithm 1
+ * (non-redundant sampling: overlapping volumes share points) and the second
+ * pass is one batched solve over the union of the samples, each weighting
+ * masked to its own sample (lgk_solve_weightings_masked).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * lgk_low_dose_volumes -- the low-dose volumes of a result's plans.
+ * Doses d = phi_cand t of every plan on n_cand candidate points (FP64, on the
+ * device, the product lgk_fetch_doses computes), then for each of n_levels
+ * ranges [d_lo[l], d_lo[l] + delta[l]) (the upper end computed in FP64 on the
+ * host) the membership of every candidate:
+ *   phi_cand: n_cand x 24N host array (>= 0); streamed to the device in chunks.
+ *   member:   n_levels x K x ceil(n_cand/32) uint32 (host, output); candidate i
+ *             is in volume (l, j) when bit (i % 32) of word i / 32 of row (l, j)
+ *             is set.
+ *   count:    n_levels x K (host, output): |V_lj|.
+ * 1 <= n_levels <= 8, d_lo > 0, delta > 0; LGK_EINVAL otherwise.
+ */
+int lgk_low_dose_volumes(const lgk_result* res, const double* phi_cand, int n_cand, int n_levels,
+                         const double* d_lo, const double* delta, uint32_t* member, int* count);
+
+/*
+ * lgk_sample_low_dose -- Algorithm 1 (Sec. 2.C), on the host.
+ * Volumes V_j (j < K) are candidate bitsets (member: K x ceil(n_cand/32), as
+ * lgk_low_dose_volumes writes one level).  Volume j wants n_desired[j] points
+ * (capped at |V_j|), i.e. sampling density w_j = n_desired[j] / |V_j|.  The
+ * volumes are visited by decreasing w_j (ties: smaller j; empty volumes are
+ * skipped); at each one the union's current points are thinned to w_j times
+ * the union volume, those inside V_j are reused, and w_j times the new part
+ * of V_j is drawn fresh.  Counts are w_j x (a set size) rounded to nearest,
+ * halves up, in exact integer arithmetic.  A draw of k items from a set takes
+ * the k items with the smallest keys
+ *     key(i) = f(f(f(f(seed) ^ level) ^ (2 j + s)) ^ i)
+ * (f = the SplitMix64 output function of Steele, Lea and Flood, 2014; s = 0
+ * for the thinning draw, 1 for the fresh draw; i = candidate index), so the
+ * result is a deterministic function of the inputs.
+ * Outputs (host): *n_union = |P|, P the union of the samples p_j;
+ * union_idx[0..n_union) its candidate indices, ascending (capacity n_cand);
+ * sel (may be NULL): n_union x ceil(K/32) uint32, bit j of row u set when
+ * union point u belongs to p_j (capacity n_cand x ceil(K/32)).
+ */
+int lgk_sample_low_dose(int K, int n_cand, const uint32_t* member, const int* n_desired, uint64_t seed,
+                        int level, int* n_union, int* union_idx, uint32_t* sel);
+
+typedef struct {
+    const double* phi_cand;  /* n_cand x 24N host: dose-rate kernels of the candidate points
+                                of the second pass's low-dose volumes                        */
+    int n_cand;
+    double delta_ld1;        /* Delta of the LD1 and LD2 volumes [D_LD, D_LD + Delta), Gy    */
+    double delta_ld2;
+    int n_ld1, n_ld2;        /* desired points per weighting and level; <= 0: the first
+                                pass's LD1 / LD2 point counts                                 */
+    uint64_t seed;           /* Algorithm 1 draws (level 0: LD1, level 1: LD2)               */
+} lgk_pass2_params;
+
+/*
+ * lgk_two_pass -- both passes in one call.
+ * Pass 1: lgk_create_case(desc, p) and lgk_solve_weightings with the rho rule
+ * (Eq. rho_rule) and rho0 = rho0_per_beta x beta of that case.  Then the
+ * LD1 and LD2 volumes of every plan on the candidates, Algorithm 1 per level
+ * (desired counts as above), and pass 2: a case whose points are desc's
+ * non-low-dose points (in order), then the LD1 union points, then the LD2
+ * union points (candidate order), solved with lgk_solve_weightings_masked
+ * (rho0 = rho0_per_beta x beta of the second case, same W, tol, max_iter).
+ * Outputs: *res1_out (may be NULL: freed), *case2_out and *res2_out (owned by
+ * the caller), n_union[2] and union_idx[2][n_cand] (candidate indices of the
+ * LD1 and LD2 union points; either may be NULL).  On error every output
+ * handle is NULL.
+ */
+int lgk_two_pass(const lgk_case_desc* desc, const lgk_params* p, int K, const double* W, double w0_bot,
+                 double rho0_per_beta, double tol, int max_iter, const lgk_pass2_params* p2,
+                 lgk_result** res1_out, lgk_case** case2_out, lgk_result** res2_out, int* n_union,
+                 int* union_idx);
 
 /* ADMM state of the scaled problem in q-form: q1 = z1 + y1 (K x n) and
  * q2 = z2 + y2 (K x m), FP64 host arrays (either may be NULL).  Feeding them

@@ -14,8 +14,10 @@ Modules (each function cites the passage of arXiv 2509.08602 it follows):
   vertex   -- brute-force vertex enumeration for tiny LPs
   kkt      -- optimality (KKT) residuals and the primal objective of Sec. 2.A
   metrics  -- dose and clinical metrics (Sec. 2.A, Sec. 3.B)
+  sampling -- second-pass low-dose volumes and Algorithm 1 (Sec. 2.C), with
+              the SplitMix64 counter-based draws both sides implement
 
 Parity status: every function here is pinned by `tests/test_oracle_*.py`
-against closed forms, brute force, a library LP solver (HiGHS via scipy) or
-invariants; none is "parity unpinned".
+against closed forms, brute force, a library LP solver (HiGHS via scipy),
+published generator outputs or invariants; none is "parity unpinned".
 """

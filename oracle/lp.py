@@ -145,7 +145,7 @@ def precondition(lp: DualLP, *, normalize_rows=True, scale_bot=True) -> DualLP:
     return dataclasses.replace(lp, A=A, row_scale=d_r, beta=beta)
 
 
-def bounds(lp: DualLP, W) -> tuple:
+def bounds(lp: DualLP, W, select=None) -> tuple:
     """Per-weighting (b, l, u) columns (Appendix A), each (m or n) x K.
 
     u = (w_TS/N_TS, w_TI/N_TI, w_R/N_R, w_LD/N_LD, inf, inf); with several
@@ -153,17 +153,29 @@ def bounds(lp: DualLP, W) -> tuple:
     normalised by that target's own point count.  Each low-dose volume (LD1,
     LD2) gets w_LD over its own point count.  b = (0, w_BOT), times the row
     scale D_r when the rows were normalised.
+
+    select (n_pts, K) bool, optional: the dose points each weighting keeps
+    (Sec. 2.C, second pass); the others get u = 0, and each class's point
+    count is the count of its selected points in that weighting.
     """
     W = np.atleast_2d(np.asarray(W, dtype=np.float64))
     K = W.shape[0]
     qa, qv = lp.q_area, lp.q_vol
     nT = lp.n_targets
     u = np.full((lp.n, K), np.inf)
+    if select is None:
+        select = np.ones((lp.n_pts, K), dtype=bool)
+    select = np.asarray(select, dtype=bool)
+    counts = {}
+    for j in range(lp.n_pts):
+        key = (int(lp.kind[j]), int(lp.struct_id[j]))
+        counts[key] = counts.get(key, 0) + select[j].astype(np.int64)
     for j in range(lp.n):
         k, s = int(lp.kind[j]), int(lp.struct_id[j])
         if k < 0 or k == OAR:
             continue
-        cnt = lp.counts[(k, s)]
+        cnt = counts[(k, s)].astype(np.float64)
+        cnt[cnt == 0] = np.inf       # a class with no selected point: u = 0
         wT, wR, wLD = W[:, 0], W[:, 1], W[:, 2]
         if k == TS:
             u[j] = qa[s] * wT / cnt
@@ -173,6 +185,7 @@ def bounds(lp: DualLP, W) -> tuple:
             u[j] = (wR / nT) / cnt
         else:  # LD1, LD2
             u[j] = wLD / cnt
+        u[j] = np.where(select[j], u[j], 0.0)
     l = np.zeros((lp.n, K))
     b = np.zeros((lp.m, K))
     b[lp.n_beams:, :] = W[:, 3][None, :]

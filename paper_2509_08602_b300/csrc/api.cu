@@ -149,9 +149,9 @@ int lgk_case_info(const lgk_case* c, int* m, int* n, double* beta, size_t* bytes
     return LGK_OK;
 }
 
-int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
-                              double rho0, double tol, int max_iter, const double* q1_init,
-                              const double* q2_init, lgk_result** out) {
+int lgk_solve_weightings_masked(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
+                                double rho0, double tol, int max_iter, const uint32_t* mask,
+                                const double* q1_init, const double* q2_init, lgk_result** out) {
     if (!out) return fail(LGK_EINVAL, "out is NULL");
     *out = nullptr;
     if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
@@ -186,7 +186,7 @@ int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double*
         return fail(LGK_EINVAL, "initial state must be finite");
     int rc;
     try {
-        rc = run_solve(*res, W, r.data(), q1_init, q2_init);
+        rc = run_solve(*res, W, r.data(), q1_init, q2_init, mask);
     } catch (const std::bad_alloc&) {
         rc = fail(LGK_ENOMEM, "host allocation failed");
     }
@@ -198,9 +198,17 @@ int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double*
     return LGK_OK;
 }
 
+int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
+                              double rho0, double tol, int max_iter, const double* q1_init,
+                              const double* q2_init, lgk_result** out) {
+    return lgk_solve_weightings_masked(c, K, W, rho, w0_bot, rho0, tol, max_iter, nullptr, q1_init,
+                                       q2_init, out);
+}
+
 int lgk_solve_weightings(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
                          double rho0, double tol, int max_iter, lgk_result** out) {
-    return lgk_solve_weightings_warm(c, K, W, rho, w0_bot, rho0, tol, max_iter, nullptr, nullptr, out);
+    return lgk_solve_weightings_masked(c, K, W, rho, w0_bot, rho0, tol, max_iter, nullptr, nullptr,
+                                       nullptr, out);
 }
 
 int lgk_fetch_times(const lgk_result* r, double* t, double* tau) {
@@ -215,6 +223,19 @@ int lgk_fetch_doses(const lgk_result* r, const double* phi_eval, int n_eval, dou
         return fail(LGK_EINVAL, "phi_eval must be finite and >= 0");
     LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
     return fetch_doses(*r->d, phi_eval, n_eval, dose);
+}
+
+int lgk_fetch_metrics(const lgk_result* r, const double* phi_eval, int n_eval, const int* label,
+                      double* coverage, double* selectivity, double* gi, double* bot) {
+    if (!r || !phi_eval || !label || n_eval < 1) return fail(LGK_EINVAL, "bad fetch_metrics arguments");
+    const CaseData& cs = *r->d->cs;
+    if (!finite_nonneg(phi_eval, (size_t)n_eval * cs.n_beams))
+        return fail(LGK_EINVAL, "phi_eval must be finite and >= 0");
+    for (int e = 0; e < n_eval; ++e)
+        if (label[e] < -1 || label[e] >= cs.n_targets)
+            return fail(LGK_EINVAL, "label " + std::to_string(e) + " out of range");
+    LGK_CUDA_TRY(cudaSetDevice(cs.device));
+    return fetch_metrics(*r->d, phi_eval, n_eval, label, coverage, selectivity, gi, bot);
 }
 
 int lgk_fetch_stats(const lgk_result* r, int* iters, double* obj, double* rel_pri, double* rel_dual,

@@ -112,7 +112,7 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
     int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (p >= cx.n_pad) return;
     int sl = cx.col_slot[p];
-    float u = cx.utab[j * cx.n_slot + sl];
+    float u = u_at(cx, p, sl, j);
     float cr = cx.c_slot[sl] * cx.inv_rho[j];
     float q = cx.q1[(size_t)j * cx.n_pad + p];
     float z = fminf(fmaxf(q, 0.f), u);
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128) k_q1_update(IterCtx cx, SumSrc src, void*
     const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
     const size_t o = (size_t)j * cx.n_pad + p;
     const int sl = cx.col_slot[p];
-    Q1Update q = q1_update(cx.q1[o], gemm_out(src, p, j), cx.utab[j * cx.n_slot + sl],
+    Q1Update q = q1_update(cx.q1[o], gemm_out(src, p, j), u_at(cx, p, sl, j),
                            cx.c_slot[sl] * cx.inv_rho[j]);
     if (cx.active[j]) cx.q1[o] = q.qn;
     if (BF16) {
@@ -301,7 +301,7 @@ __global__ void k_objective(IterCtx cx, double* obj) {
     double s = 0.0;
     for (int p = threadIdx.x; p < cx.n_pad; p += 256) {
         int sl = cx.col_slot[p];
-        float u = cx.utab[j * cx.n_slot + sl];
+        float u = u_at(cx, p, sl, j);
         float z = fminf(fmaxf(cx.q1[(size_t)j * cx.n_pad + p], 0.f), u);
         s += (double)cx.c_slot[sl] * (double)z;
     }
@@ -341,6 +341,8 @@ static IterCtx make_ctx(ResultData& r) {
     cx.tol = (float)r.tol;
     cx.col_slot = cs.col_slot.as<uint8_t>();
     cx.utab = r.utab.as<float>();
+    cx.mask = r.mask_words ? r.mask.as<uint32_t>() : nullptr;
+    cx.mask_words = r.mask_words;
     cx.c_slot = r.utab.as<float>() + (size_t)r.Kp * cs.n_slot;
     cx.rho = r.colp.as<float>();
     cx.inv_rho = r.colp.as<float>() + r.Kp;
@@ -442,7 +444,7 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
 }
 
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init) {
+              const double* q2_init, const uint32_t* mask) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
     const bool bf16 = cs.prm.precision != LGK_PREC_FP32;
@@ -457,18 +459,40 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.n_tile_s = r.n_tile > 128 ? r.n_tile / 2 : r.n_tile;
     const int Kp = r.Kp, T = cs.n_targets, S = cs.n_slot;
 
+    // point selection per column (second pass, Sec. 2.C): device layout
+    // [n_pad][mw] words, rows past the points (BOT columns, padding) all set;
+    // the point counts N_alpha that normalise u are the selected counts
+    const int mw = (Kp + 31) / 32;
+    std::vector<int> cnt((size_t)K * S);
+    for (int j = 0; j < K; ++j) std::copy(cs.slot_count.begin(), cs.slot_count.end(), &cnt[(size_t)j * S]);
+    std::vector<uint32_t> mdev;
+    if (mask) {
+        const int cw = (K + 31) / 32;
+        mdev.assign((size_t)cs.n_pad * mw, 0xffffffffu);
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int p = 0; p < cs.n_pts; ++p) {
+            uint32_t* row = &mdev[(size_t)p * mw];
+            for (int w = 0; w < mw; ++w) row[w] = w < cw ? mask[(size_t)p * cw + w] : 0u;
+            if (cw * 32 > K) row[cw - 1] &= (K % 32) ? ((1u << (K % 32)) - 1u) : 0xffffffffu;
+            const int sl = cs.slot_host[p];
+            for (int j = 0; j < K; ++j) cnt[(size_t)j * S + sl] += (row[j >> 5] >> (j & 31)) & 1u;
+        }
+    }
+    r.mask_words = mask ? mw : 0;
+
     // per-column tables (Appendix A bounds; Eq. rho_rule or caller rho)
     std::vector<float> utab((size_t)Kp * S + S, 0.0f), colp((size_t)4 * Kp, 0.0f);
     for (int j = 0; j < K; ++j) {
         double wT = W[4 * j], wR = W[4 * j + 1], wLD = W[4 * j + 2], wB = W[4 * j + 3];
         float* u = &utab[(size_t)j * S];
+        const int* nc = &cnt[(size_t)j * S];
         for (int k = 0; k < T; ++k) {
-            u[3 * k] = cs.slot_count[3 * k] ? (float)(cs.q_area[k] * wT / cs.slot_count[3 * k]) : 0.f;
-            u[3 * k + 1] = cs.slot_count[3 * k + 1] ? (float)(cs.q_vol[k] * wT / cs.slot_count[3 * k + 1]) : 0.f;
-            u[3 * k + 2] = cs.slot_count[3 * k + 2] ? (float)((wR / T) / cs.slot_count[3 * k + 2]) : 0.f;
+            u[3 * k] = nc[3 * k] ? (float)(cs.q_area[k] * wT / nc[3 * k]) : 0.f;
+            u[3 * k + 1] = nc[3 * k + 1] ? (float)(cs.q_vol[k] * wT / nc[3 * k + 1]) : 0.f;
+            u[3 * k + 2] = nc[3 * k + 2] ? (float)((wR / T) / nc[3 * k + 2]) : 0.f;
         }
-        u[slot_ld1(T)] = cs.slot_count[slot_ld1(T)] ? (float)(wLD / cs.slot_count[slot_ld1(T)]) : 0.f;
-        u[slot_ld2(T)] = cs.slot_count[slot_ld2(T)] ? (float)(wLD / cs.slot_count[slot_ld2(T)]) : 0.f;
+        u[slot_ld1(T)] = nc[slot_ld1(T)] ? (float)(wLD / nc[slot_ld1(T)]) : 0.f;
+        u[slot_ld2(T)] = nc[slot_ld2(T)] ? (float)(wLD / nc[slot_ld2(T)]) : 0.f;
         u[slot_oar(T)] = INFINITY;
         u[slot_bot(T)] = INFINITY;
         u[slot_pad(T)] = 0.f;
@@ -487,6 +511,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if (!bf16 && (rc = r.W.alloc(nq * 4))) return rc;
     if (!bf16 && (rc = r.part.alloc(mq * 4))) return rc;     // BF16 forms: tc_prepare
     if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
+    if (mask && (rc = r.mask.alloc(mdev.size() * 4))) return rc;
     if ((rc = r.active.alloc((size_t)2 * Kp * 4)) || (rc = r.iters.alloc((size_t)Kp * 4))) return rc;
     if ((rc = r.ctrl.alloc(sizeof(Control)))) return rc;
     r.n_resid_n = cs.n_pad / 128;
@@ -499,6 +524,8 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     Control c0{0, K, r.max_iter, 0, 0};
     LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
+    if (mask)
+        LGK_CUDA_TRY(cudaMemcpyAsync(r.mask.p, mdev.data(), mdev.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.active.p, act.data(), act.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.ctrl.p, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemsetAsync(r.iters.p, 0, r.iters.bytes, st));
@@ -643,6 +670,109 @@ int times_into(const ResultData& r, double* t_dev) {
     dim3 g((cs.n_beams + 255) / 256, r.K);
     k_times_into<<<g, 256, 0, cs.stream>>>(cx, r.K, t_dev);
     LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
+// Metric counts of plan j over the evaluation points: [0] covered target
+// points, [1] points >= min prescription, [2] points >= D/2, [3] points >= D
+// (D the common prescription), [4] target points.  Integer atomics: the
+// counts do not depend on the order of the additions.
+__global__ void k_metric_counts(const double* __restrict__ dose, const int* __restrict__ label,
+                                const double* __restrict__ d_presc, double d_min, double d_ref,
+                                int n_eval, unsigned long long* counts) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    unsigned c[5] = {0, 0, 0, 0, 0};
+    if (e < n_eval) {
+        const double d = dose[(size_t)j * n_eval + e];
+        const int lab = label[e];
+        c[0] = lab >= 0 && d >= d_presc[lab];
+        c[1] = d >= d_min;
+        c[2] = d >= 0.5 * d_ref;
+        c[3] = d >= d_ref;
+        c[4] = lab >= 0;
+    }
+    __shared__ unsigned red[5][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        unsigned v = c[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        unsigned long long s = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[threadIdx.x][i];
+        atomicAdd(&counts[(size_t)j * 5 + threadIdx.x], s);
+    }
+}
+
+// Beam-on time of plan j (Sec. 3.B): per isocenter the longest sector, its
+// three collimator times summed; summed over isocenters in a fixed order.
+__global__ void k_beam_on_time(const double* __restrict__ t, int n_iso, double* bot) {
+    const int j = blockIdx.x;
+    const double* tj = t + (size_t)j * 24 * n_iso;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n_iso; i += blockDim.x) {
+        double mx = 0.0;
+        for (int sct = 0; sct < 8; ++sct) {
+            const double* p = tj + (size_t)(i * 8 + sct) * 3;
+            mx = fmax(mx, p[0] + p[1] + p[2]);
+        }
+        s += mx;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bot[j] = red[0];
+}
+
+int fetch_metrics(const ResultData& r, const double* phi_eval, int n_eval, const int* label,
+                  double* coverage, double* selectivity, double* gi, double* bot) {
+    ResultData& rr = const_cast<ResultData&>(r);
+    CaseData& cs = *rr.cs;
+    cudaStream_t st = cs.stream;
+    const int B = cs.n_beams, K = r.K;
+    DevBuf td, pd, dd, ld, presc, cnt, botd;
+    int rc;
+    if ((rc = td.alloc((size_t)K * B * 8)) || (rc = pd.alloc((size_t)n_eval * B * 8)) ||
+        (rc = dd.alloc((size_t)K * n_eval * 8)) || (rc = ld.alloc((size_t)n_eval * 4)) ||
+        (rc = presc.alloc((size_t)cs.n_targets * 8)) || (rc = cnt.alloc((size_t)K * 5 * 8)) ||
+        (rc = botd.alloc((size_t)K * 8)))
+        return rc;
+    LGK_CUDA_TRY(cudaMemcpyAsync(pd.p, phi_eval, pd.bytes, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(ld.p, label, ld.bytes, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(presc.p, cs.d_presc.data(), presc.bytes, cudaMemcpyHostToDevice, st));
+    LGK_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, cnt.bytes, st));
+    if ((rc = times_into(r, td.as<double>()))) return rc;
+    if ((rc = dgemm(st, false, true, K, n_eval, B, 1.0, td.as<double>(), B, pd.as<double>(), B, 0.0,
+                    dd.as<double>(), n_eval)))
+        return rc;
+    double d_min = cs.d_presc[0], d_max = cs.d_presc[0];
+    for (double d : cs.d_presc) d_min = std::min(d_min, d), d_max = std::max(d_max, d);
+    dim3 g((n_eval + 255) / 256, K);
+    k_metric_counts<<<g, 256, 0, st>>>(dd.as<double>(), ld.as<int>(), presc.as<double>(), d_min,
+                                       cs.d_presc[0], n_eval, cnt.as<unsigned long long>());
+    LGK_LAUNCH_CHECK();
+    k_beam_on_time<<<K, 256, 0, st>>>(td.as<double>(), cs.n_iso, botd.as<double>());
+    LGK_LAUNCH_CHECK();
+    std::vector<unsigned long long> c((size_t)K * 5);
+    std::vector<double> b(K);
+    LGK_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, cnt.bytes, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaMemcpyAsync(b.data(), botd.p, botd.bytes, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    const bool equal = d_min == d_max;
+    for (int j = 0; j < K; ++j) {
+        const unsigned long long* q = &c[(size_t)j * 5];
+        if (coverage) coverage[j] = (double)q[0] / (double)std::max(q[4], 1ull);
+        if (selectivity) selectivity[j] = (double)q[0] / (double)std::max(q[1], 1ull);
+        if (gi) gi[j] = equal ? (double)q[2] / (double)std::max(q[3], 1ull) : NAN;
+        if (bot) bot[j] = b[j];
+    }
     return LGK_OK;
 }
 

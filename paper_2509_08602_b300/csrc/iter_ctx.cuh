@@ -11,6 +11,8 @@ struct IterCtx {
     float tol;
     const uint8_t* col_slot;
     const float* utab;      // [Kp][n_slot]
+    const uint32_t* mask;   // [n_pad][mask_words] point selection per column, or NULL (all)
+    int mask_words;
     const float* c_slot;    // [n_slot] (stored after utab)
     const float* rho;       // colp[0]
     const float* inv_rho;   // colp[1]
@@ -27,6 +29,14 @@ struct IterCtx {
     double eps_abs;
     int n, m_rows;
 };
+
+// Upper bound u of point p (slot sl) in column j: the slot's bound, or 0 where
+// the column's point selection leaves p out (Sec. 2.C, second pass).
+__device__ inline float u_at(const IterCtx& cx, int p, int sl, int j) {
+    float u = cx.utab[j * cx.n_slot + sl];
+    if (cx.mask && !((cx.mask[(size_t)p * cx.mask_words + (j >> 5)] >> (j & 31)) & 1u)) u = 0.f;
+    return u;
+}
 
 __device__ inline bool is_check_iter(const Control* c, int check_every, float tol) {
     int it = c->iter + 1;

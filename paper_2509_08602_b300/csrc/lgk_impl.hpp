@@ -36,7 +36,8 @@ struct CaseData {
     int n_targets = 0, n_oars = 0, n_slot = 0;
     double beta = 1.0;
     std::vector<int> slot_count;           // points per slot (TS/TI/R per target, LD1, LD2, OAR)
-    std::vector<double> q_area, q_vol;
+    std::vector<uint8_t> slot_host;        // slot of every point [n_pts]
+    std::vector<double> q_area, q_vol, d_presc;
     std::vector<float> c_of_slot;          // c per slot (Appendix A: -1, -1, +1, +1, +1, 0)
 
     DevBuf col_slot;   // uint8 [n_pad]
@@ -87,6 +88,8 @@ struct ResultData {
     DevBuf part;              // float segment partial sums [slot][n_tile][128] (BF16 forms), or
                               // one GEMM output [Kp][rows] (FP32 form)
     DevBuf utab;              // float [Kp][n_slot] upper bounds u per slot
+    DevBuf mask;              // uint32 [n_pad][mask_words] point selection, when given
+    int mask_words = 0;       // 0: every point in every column
     DevBuf colp;              // float [4][Kp]: rho, 1/rho, w_BOT, unused
     DevBuf active, iters;     // int [Kp]
     DevBuf ctrl;              // Control
@@ -108,13 +111,15 @@ int setup_case(CaseData& cs, const lgk_case_desc& d);
 
 // one solve (iter.cu)
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init);
+              const double* q2_init, const uint32_t* mask);
 int fetch_times(const ResultData& r, double* t, double* tau);
 int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double* dose);
 int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri,
                 double* rel_dual, uint8_t* converged);
 int fetch_state(const ResultData& r, double* q1, double* q2);
 int times_into(const ResultData& r, double* t_dev);   // K x n_beams FP64, device
+int fetch_metrics(const ResultData& r, const double* phi_eval, int n_eval, const int* label,
+                  double* coverage, double* selectivity, double* gi, double* bot);
 
 // FP64 GEMM (setup.cu):  C = alpha op(A) op(B) + beta C, row-major.
 int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,

@@ -367,6 +367,7 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
         scale[p] = sign / D;
         cs.slot_count[sl] += 1;
     }
+    cs.slot_host.assign(slot.begin(), slot.begin() + P);
     for (int q = P; q < n; ++q) slot[q] = (uint8_t)slot_bot(T);
     cs.c_of_slot.assign(cs.n_slot, 0.0f);
     for (int k = 0; k < T; ++k) {
@@ -379,6 +380,7 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
     cs.c_of_slot[slot_oar(T)] = 1.0f;
     cs.q_area.assign(d.q_area, d.q_area + T);
     cs.q_vol.assign(d.q_vol, d.q_vol + T);
+    cs.d_presc.assign(d.d_presc, d.d_presc + T);
     int n_cost = 0;
     for (int p = 0; p < P; ++p) n_cost += d.kind[p] != LGK_OAR;
     cs.beta = cs.prm.scale_bot ? n_cost / 2000.0 : 1.0;

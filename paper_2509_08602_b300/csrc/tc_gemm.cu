@@ -213,6 +213,7 @@ enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3 };
 constexpr int kThreads = 320;               // 2 producer/MMA warps + 8 epilogue warps
 constexpr int kEpiThreads = 256;
 constexpr int kChunk = 8;                   // columns per epilogue step
+static_assert(32 % kChunk == 0, "a chunk's columns must share one point-selection word");
 constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile
 
 __device__ inline void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -284,10 +285,13 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         const float c_p = cx.c_slot[sl];
         float q[kChunk], u[kChunk], ir[kChunk];
         int act[kChunk];
+        // the chunk's 8 columns share one word of the point selection (j0 % 8 == 0)
+        const uint32_t sel =
+            cx.mask ? __ldg(cx.mask + (size_t)row * cx.mask_words + (j0 >> 5)) >> (j0 & 31) : 0xffu;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             q[c] = q1p[(size_t)c * cx.n_pad];
-            u[c] = __ldg(cx.utab + (j0 + c) * cx.n_slot + sl);
+            u[c] = ((sel >> c) & 1u) ? __ldg(cx.utab + (j0 + c) * cx.n_slot + sl) : 0.0f;
             ir[c] = __ldg(cx.inv_rho + j0 + c);
             act[c] = cx.active[j0 + c];
         }

@@ -52,6 +52,12 @@ class ServerParams(C.Structure):
                 ("rho0_per_beta", C.c_double)]
 
 
+class Pass2Params(C.Structure):
+    _fields_ = [("phi_cand", C.POINTER(C.c_double)), ("n_cand", C.c_int), ("delta_ld1", C.c_double),
+                ("delta_ld2", C.c_double), ("n_ld1", C.c_int), ("n_ld2", C.c_int),
+                ("seed", C.c_uint64)]
+
+
 class RequestInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("K", C.c_int), ("n_iso", C.c_int), ("queue_ms", C.c_double),
                 ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("total_ms", C.c_double),
@@ -76,7 +82,21 @@ def _load():
     lib.lgk_solve_weightings_warm.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
                                               C.c_double, C.c_double, C.c_double, C.c_int,
                                               P(C.c_double), P(C.c_double), P(C.c_void_p)]
+    lib.lgk_solve_weightings_masked.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
+                                                C.c_double, C.c_double, C.c_double, C.c_int,
+                                                P(C.c_uint32), P(C.c_double), P(C.c_double),
+                                                P(C.c_void_p)]
+    lib.lgk_low_dose_volumes.argtypes = [C.c_void_p, P(C.c_double), C.c_int, C.c_int, P(C.c_double),
+                                         P(C.c_double), P(C.c_uint32), P(C.c_int)]
+    lib.lgk_sample_low_dose.argtypes = [C.c_int, C.c_int, P(C.c_uint32), P(C.c_int), C.c_uint64,
+                                        C.c_int, P(C.c_int), P(C.c_int), P(C.c_uint32)]
+    lib.lgk_two_pass.argtypes = [P(CaseDesc), P(Params), C.c_int, P(C.c_double), C.c_double,
+                                 C.c_double, C.c_double, C.c_int, P(Pass2Params), P(C.c_void_p),
+                                 P(C.c_void_p), P(C.c_void_p), P(C.c_int), P(C.c_int)]
     lib.lgk_fetch_profile.argtypes = [C.c_void_p, P(C.c_double), P(C.c_longlong)]
+    lib.lgk_fetch_metrics.argtypes = [C.c_void_p, P(C.c_double), C.c_int, P(C.c_int), P(C.c_double),
+                                       P(C.c_double), P(C.c_double), P(C.c_double)]
+    lib.lgk_fetch_metrics.restype = C.c_int
     lib.lgk_fetch_doses_device.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
     lib.lgk_fetch_doses_device.restype = C.c_int
     lib.lgk_server_create.argtypes = [P(ServerParams), P(C.c_void_p)]
@@ -137,6 +157,13 @@ class Case:
         self.close()
 
 
+class _Dims:
+    """Sizes of a case held only by its results."""
+
+    def __init__(self, m: int, n: int):
+        self.m, self.n = m, n
+
+
 class Result:
     """Solved batch of weightings (lgk_result)."""
 
@@ -177,22 +204,7 @@ def _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi
 
 def create_case(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal,
                 d_oar=None, params: Params | None = None) -> Case:
-    phi = np.ascontiguousarray(phi, dtype=np.float64)
-    kind = np.ascontiguousarray(kind, dtype=np.uint8)
-    struct_id = np.ascontiguousarray(struct_id, dtype=np.uint16)
-    d_presc = np.ascontiguousarray(np.atleast_1d(d_presc), dtype=np.float64)
-    q_area = np.ascontiguousarray(np.atleast_1d(q_area), dtype=np.float64)
-    q_vol = np.ascontiguousarray(np.atleast_1d(q_vol), dtype=np.float64)
-    d_oar = None if d_oar is None or len(d_oar) == 0 else np.ascontiguousarray(d_oar, dtype=np.float64)
-    d = CaseDesc(n_iso=int(n_iso), n_pts=int(phi.shape[0]), n_targets=int(d_presc.shape[0]),
-                 n_oars=0 if d_oar is None else int(d_oar.shape[0]),
-                 phi=_ptr(phi, C.c_double), kind=_ptr(kind, C.c_uint8),
-                 struct_id=_ptr(struct_id, C.c_uint16), d_presc=_ptr(d_presc, C.c_double),
-                 q_area=_ptr(q_area, C.c_double), q_vol=_ptr(q_vol, C.c_double),
-                 d_oar=_ptr(d_oar, C.c_double), d_ld1=float(d_ld1), d_ld2=float(d_ld2),
-                 phi_cal=float(phi_cal))
-    if phi.shape[1] != 24 * int(n_iso) or kind.shape[0] != phi.shape[0] or struct_id.shape[0] != phi.shape[0]:
-        raise LgkError(1, "phi must be n_pts x 24 n_iso; kind and struct_id of length n_pts")
+    d, _keep = _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal, d_oar)
     h = C.c_void_p()
     _check(_lib.lgk_create_case(C.byref(d), C.byref(params) if params is not None else None,
                                 C.byref(h)))
@@ -231,6 +243,102 @@ def solve_weightings_warm(case: Case, W, rho=None, *, q1_init=None, q2_init=None
     return Result(h, K, case)
 
 
+def pack_bits(sel) -> np.ndarray:
+    """(rows, K) bool -> (rows, ceil(K/32)) uint32, bit j % 32 of word j / 32."""
+    sel = np.asarray(sel, dtype=bool)
+    rows, K = sel.shape
+    kw = (K + 31) // 32
+    pad = np.zeros((rows, kw * 32), dtype=bool)
+    pad[:, :K] = sel
+    return np.ascontiguousarray(np.packbits(pad, axis=1, bitorder="little").view("<u4"))
+
+
+def unpack_bits(words, K: int) -> np.ndarray:
+    """Inverse of pack_bits: (rows, ceil(K/32)) uint32 -> (rows, K) bool."""
+    w = np.ascontiguousarray(words, dtype="<u4")
+    return np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")[..., :K].astype(bool)
+
+
+def solve_weightings_masked(case: Case, W, rho=None, *, select=None, q1_init=None, q2_init=None,
+                            w0_bot: float = 0.0, rho0: float = 0.0, tol: float = 1e-4,
+                            max_iter: int = 10000) -> Result:
+    """Batched solve with a point selection per weighting: select is
+    (n_pts, K) bool (None: every point), packed for lgk_solve_weightings_masked."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K = W.shape[0]
+    r = None if rho is None else np.ascontiguousarray(np.broadcast_to(rho, (K,)), dtype=np.float64)
+    mask = None if select is None else pack_bits(select)
+    q1 = None if q1_init is None else np.ascontiguousarray(q1_init, dtype=np.float64)
+    q2 = None if q2_init is None else np.ascontiguousarray(q2_init, dtype=np.float64)
+    h = C.c_void_p()
+    _check(_lib.lgk_solve_weightings_masked(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double),
+                                            float(w0_bot), float(rho0), float(tol), int(max_iter),
+                                            _ptr(mask, C.c_uint32), _ptr(q1, C.c_double),
+                                            _ptr(q2, C.c_double), C.byref(h)))
+    return Result(h, K, case)
+
+
+def low_dose_volumes(res: Result, phi_cand, d_lo, delta):
+    """Membership (levels, K, n_cand) bool and sizes (levels, K) of the
+    low-dose volumes [d_lo, d_lo + delta) of every plan (Sec. 2.C)."""
+    phi_cand = np.ascontiguousarray(phi_cand, dtype=np.float64)
+    d_lo = np.ascontiguousarray(np.atleast_1d(d_lo), dtype=np.float64)
+    delta = np.ascontiguousarray(np.atleast_1d(delta), dtype=np.float64)
+    L, nc = d_lo.shape[0], phi_cand.shape[0]
+    words = (nc + 31) // 32
+    member = np.zeros((L, res.K, words), dtype=np.uint32)
+    count = np.zeros((L, res.K), dtype=np.int32)
+    _check(_lib.lgk_low_dose_volumes(res._h, _ptr(phi_cand, C.c_double), nc, L, _ptr(d_lo, C.c_double),
+                                     _ptr(delta, C.c_double), _ptr(member, C.c_uint32),
+                                     _ptr(count, C.c_int)))
+    return unpack_bits(member, nc), count
+
+
+def sample_low_dose(member, n_desired, seed: int, level: int = 0):
+    """Algorithm 1 (Sec. 2.C) on volumes member (K, n_cand) bool.  Returns
+    (union candidate indices ascending, sel (n_union, K) bool)."""
+    member = np.asarray(member, dtype=bool)
+    K, nc = member.shape
+    words = pack_bits(member)
+    nd = np.ascontiguousarray(np.broadcast_to(n_desired, (K,)), dtype=np.int32)
+    kw = (K + 31) // 32
+    n_union = C.c_int()
+    idx = np.zeros(nc, dtype=np.int32)
+    sel = np.zeros((nc, kw), dtype=np.uint32)
+    _check(_lib.lgk_sample_low_dose(K, nc, _ptr(words, C.c_uint32), _ptr(nd, C.c_int),
+                                    C.c_uint64(int(seed) & (2 ** 64 - 1)), int(level), C.byref(n_union),
+                                    _ptr(idx, C.c_int), _ptr(sel, C.c_uint32)))
+    nu = n_union.value
+    return idx[:nu].copy(), unpack_bits(sel[:nu], K)
+
+
+def two_pass(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal, W, *,
+             phi_cand, delta_ld1, delta_ld2, w0_bot, rho0_per_beta, n_ld1=0, n_ld2=0, seed=0,
+             d_oar=None, tol=1e-4, max_iter=10000, params: Params | None = None):
+    """Both passes of Sec. 2.C (lgk_two_pass).  Returns (res1, case2, res2,
+    (ld1 union candidate indices, ld2 union candidate indices))."""
+    d, _keep = _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal, d_oar)
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K = W.shape[0]
+    pc = np.ascontiguousarray(phi_cand, dtype=np.float64)
+    nc = pc.shape[0]
+    p2 = Pass2Params(phi_cand=_ptr(pc, C.c_double), n_cand=nc, delta_ld1=float(delta_ld1),
+                     delta_ld2=float(delta_ld2), n_ld1=int(n_ld1), n_ld2=int(n_ld2),
+                     seed=int(seed) & (2 ** 64 - 1))
+    r1, c2, r2 = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    nu = np.zeros(2, dtype=np.int32)
+    idx = np.zeros((2, nc), dtype=np.int32)
+    _check(_lib.lgk_two_pass(C.byref(d), C.byref(params) if params is not None else None, K,
+                             _ptr(W, C.c_double), float(w0_bot), float(rho0_per_beta), float(tol),
+                             int(max_iter), C.byref(p2), C.byref(r1), C.byref(c2), C.byref(r2),
+                             _ptr(nu, C.c_int), _ptr(idx, C.c_int)))
+    # the first case lives on inside res1 (the library keeps it alive)
+    case1 = _Dims(m=25 * int(n_iso), n=int(np.asarray(phi).shape[0]) + 8 * int(n_iso))
+    res1 = Result(r1, K, case1)
+    case2 = Case(c2, None)
+    return res1, case2, Result(r2, K, case2), (idx[0, :nu[0]].copy(), idx[1, :nu[1]].copy())
+
+
 def fetch_times(res: Result):
     """(t (K x 24N), tau (K x N)) as FP64."""
     n_iso = (res.case.m) // 25
@@ -254,6 +362,19 @@ def fetch_doses_device(res: Result, phi_eval_ptr: int, n_eval: int, dose_ptr: in
     dose K x n_eval FP64 out.  See lgk_fetch_doses_device in include/lgk.h."""
     _check(_lib.lgk_fetch_doses_device(res._h, C.c_void_p(phi_eval_ptr), int(n_eval),
                                        C.c_void_p(dose_ptr)))
+
+
+def fetch_metrics(res: Result, phi_eval, label) -> dict:
+    """Coverage, selectivity, gradient index and beam-on time of every plan,
+    computed on the device (Sec. 2.A, Sec. 3.B)."""
+    phi_eval = np.ascontiguousarray(phi_eval, dtype=np.float64)
+    label = np.ascontiguousarray(label, dtype=np.int32)
+    out = {k: np.empty(res.K) for k in ("coverage", "selectivity", "gi", "bot")}
+    _check(_lib.lgk_fetch_metrics(res._h, _ptr(phi_eval, C.c_double), int(phi_eval.shape[0]),
+                                  _ptr(label, C.c_int), _ptr(out["coverage"], C.c_double),
+                                  _ptr(out["selectivity"], C.c_double), _ptr(out["gi"], C.c_double),
+                                  _ptr(out["bot"], C.c_double)))
+    return out
 
 
 def fetch_stats(res: Result) -> dict:

@@ -78,6 +78,12 @@ def test_null_arguments_are_errors_not_crashes(lgk):
     assert lib.lgk_fetch_times(None, None, None) == 1
     assert lib.lgk_fetch_stats(None, None, None, None, None, None) == 1
     assert lib.lgk_default_params(None) == 1
+    assert lib.lgk_fetch_metrics(None, None, 0, None, None, None, None, None) == 1
+    assert lib.lgk_low_dose_volumes(None, None, 0, 0, None, None, None, None) == 1
+    assert lib.lgk_two_pass(None, None, 1, None, 0.0, 0.0, 0.0, 1, None, None, ctypes.byref(h),
+                            ctypes.byref(h), None, None) == 1
+    assert lib.lgk_solve_weightings_masked(None, 1, None, None, 0.0, 0.0, 0.0, 1, None, None, None,
+                                           ctypes.byref(h)) == 1
     lib.lgk_free_result(None)
     lib.lgk_destroy_case(None)
     assert b"NULL" in lib.lgk_last_error() or len(lib.lgk_last_error()) > 0

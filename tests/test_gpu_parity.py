@@ -234,3 +234,51 @@ def test_budget_and_timeout_errors(lgk, cfg0):
     cs2 = make(lgk, c["case"], 2)
     res = lgk.solve_weightings(cs2, c["W"], c["rho"], tol=0.0, max_iter=5)
     assert np.all(lgk.fetch_stats(res)["iters"] == 5)
+
+
+def _metric_check(lgk, res, case, phi_eval, label):
+    """Device metrics against the oracle's definitions on the same FP64 doses:
+    the threshold decisions are taken on identical values, so the counts (and
+    coverage, selectivity, GI) match exactly; BOT differs only by the order of
+    an FP64 sum."""
+    dose = lgk.fetch_doses(res, phi_eval)
+    t, _ = lgk.fetch_times(res)
+    met = lgk.fetch_metrics(res, phi_eval, label)
+    ref = M.plan_metrics(dose.T, label, case.d_presc, t.T, case.n_iso)
+    for key in ("coverage", "selectivity", "gi"):
+        np.testing.assert_array_equal(met[key], ref[key], err_msg=key)
+    np.testing.assert_allclose(met["bot"], ref["bot"], rtol=1e-13, atol=0)
+    return met
+
+
+def test_device_metrics_single_target(lgk, cfg0):
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    met = _metric_check(lgk, res, c["case"], c["phi_eval"], c["label"])
+    assert np.all(np.isfinite(met["gi"])) and np.all(met["gi"] >= 1.0)
+    assert np.all((met["coverage"] > 0.5) & (met["coverage"] <= 1.0))
+    # also after a few iterations only (doses far from the prescription)
+    res5 = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=5)
+    _metric_check(lgk, res5, c["case"], c["phi_eval"], c["label"])
+
+
+def test_device_metrics_two_targets_unequal_prescriptions(lgk):
+    """Per-target prescriptions (Sec. 3.B): coverage uses each point's own
+    target dose, selectivity the lowest prescription isodose, GI undefined."""
+    targets = [(np.array([-7.0, 0, 0]), np.full(3, 5.0)), (np.array([8.0, 0, 0]), np.full(3, 4.0))]
+    case = SC.make_case(targets, n_target_pts=900, n_ring=600, n_ld1=600, n_ld2=600, n_iso=14,
+                        seed=77, d_presc=[20.0, 16.0])
+    assert case.d_presc[0] != case.d_presc[1]
+    lp = L.precondition(L.assemble_case(case))
+    W = SC.slider_weights(2)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    cs = make(lgk, case, 2)
+    res = lgk.solve_weightings(cs, W, rho, tol=1e-3, max_iter=4000)
+    pts, label, _ = SC.eval_grid(case, spacing=1.5, margin=8.0)
+    phi_eval = SC.dose_rate(pts, case.iso)
+    met = _metric_check(lgk, res, case, phi_eval, label)
+    assert np.all(np.isnan(met["gi"]))
+    # every evaluation point outside the targets: coverage 0 of 0 target points
+    far = lgk.fetch_metrics(res, phi_eval[label < 0][:50], label[label < 0][:50])
+    assert np.all(far["coverage"] == 0.0)

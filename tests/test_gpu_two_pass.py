@@ -1,0 +1,167 @@
+"""GPU parity of the two-pass optimisation (Sec. 2.C) through the C ABI:
+low-dose volumes on the device, Algorithm 1 in the library, and the masked
+second-pass solve, each against the oracle.
+
+  * volumes: bit-exact against the oracle's [D_LD, D_LD + Delta) test taken
+    on the same FP64 doses (the device's, as lgk_fetch_doses returns them:
+    floating point decides membership, so both sides decide on one value);
+  * sampling: bit-exact against oracle.sampling.algorithm1;
+  * masked iteration: one ADMM iteration from a common state, element by
+    element, within ||A||_2^2 u max|q| (the unmasked bound; a masked point
+    only clips at 0);
+  * second-pass plans: converged (tol 1e-4) with the relative objective gap
+    <= 1e-3 against the simplex optimum of each weighting's own LP, assembled
+    independently from its selected points only.
+"""
+import numpy as np
+import pytest
+
+from oracle import admm as AD
+from oracle import lp as L
+from oracle import sampling as SA
+from oracle import simplex as SX
+from synth import cases as SC
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+DELTA = (1.0, 0.5)         # Delta of the LD1 (10 Gy) and LD2 (5 Gy) volumes
+N_LD = (60, 60)            # desired low-dose points per weighting and level
+SEED = 20250910
+
+
+@pytest.fixture(scope="module")
+def lgk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_08602_b300 import build
+    build.build()
+    from paper_2509_08602_b300 import lgk as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def setup(lgk):
+    case = SC.workload_case(0)
+    W = SC.slider_weights(3)
+    pts, label, _ = SC.eval_grid(case, spacing=2.0, margin=25.0)
+    cand = pts[label < 0]
+    phi_cand = SC.dose_rate(cand, case.iso)
+    res1, case2, res2, unions = lgk.two_pass(
+        case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area, case.q_vol,
+        case.d_ld1, case.d_ld2, case.phi_cal, W, phi_cand=phi_cand, delta_ld1=DELTA[0],
+        delta_ld2=DELTA[1], n_ld1=N_LD[0], n_ld2=N_LD[1], seed=SEED, w0_bot=SC.W0_BOT,
+        rho0_per_beta=L.RHO0_PER_BETA, tol=TOL, max_iter=20000)
+    return dict(case=case, W=W, phi_cand=phi_cand, res1=res1, case2=case2, res2=res2, unions=unions)
+
+
+def test_low_dose_volumes_bit_exact(lgk, setup):
+    s = setup
+    lev = (s["case"].d_ld1, s["case"].d_ld2)
+    member, count = lgk.low_dose_volumes(s["res1"], s["phi_cand"], lev, DELTA)
+    dose = lgk.fetch_doses(s["res1"], s["phi_cand"])
+    for l in range(2):
+        for j in range(s["W"].shape[0]):
+            want = SA.low_dose_volume(dose[j], lev[l], DELTA[l])
+            assert set(np.flatnonzero(member[l, j]).tolist()) == want, (l, j)
+            assert count[l, j] == len(want)
+    assert (count > N_LD[0]).any()    # some volumes are thinned (omega < 1)
+
+
+def _pass2_points(s, member):
+    """Sampling of both levels by the oracle and the pass-2 point set."""
+    case = s["case"]
+    K = s["W"].shape[0]
+    keep = np.flatnonzero(~np.isin(case.kind, (SC.KIND_LD1, SC.KIND_LD2)))
+    P, samples = [], []
+    for l in range(2):
+        Pl, pl = SA.algorithm1([set(np.flatnonzero(member[l, j]).tolist()) for j in range(K)],
+                               [N_LD[l]] * K, seed=SEED, level=l)
+        P.append(np.array(Pl, dtype=int))
+        samples.append(pl)
+    phi2 = np.concatenate([case.phi[keep], s["phi_cand"][P[0]], s["phi_cand"][P[1]]])
+    kind2 = np.concatenate([case.kind[keep], np.full(len(P[0]), SC.KIND_LD1, np.uint8),
+                            np.full(len(P[1]), SC.KIND_LD2, np.uint8)])
+    sid2 = np.concatenate([case.struct_id[keep], np.zeros(len(P[0]) + len(P[1]), np.uint16)])
+    select = np.ones((len(keep) + len(P[0]) + len(P[1]), K), bool)
+    for l, off in ((0, len(keep)), (1, len(keep) + len(P[0]))):
+        for j in range(K):
+            select[off:off + len(P[l]), j] = np.isin(P[l], sorted(samples[l][j]))
+    return P, phi2, kind2, sid2, select
+
+
+def _lp2(case, phi2, kind2, sid2):
+    return L.precondition(L.assemble(phi2, kind2, sid2, case.n_iso, case.d_presc, case.d_ld1,
+                                     case.d_ld2, case.phi_cal, case.d_oar, q_area=case.q_area,
+                                     q_vol=case.q_vol))
+
+
+def test_two_pass_sampling_and_plans(lgk, setup):
+    s = setup
+    case, W = s["case"], s["W"]
+    K = W.shape[0]
+    lev = (case.d_ld1, case.d_ld2)
+    member, _ = lgk.low_dose_volumes(s["res1"], s["phi_cand"], lev, DELTA)
+    P, phi2, kind2, sid2, select = _pass2_points(s, member)
+    # the library's union points are the oracle's
+    assert s["unions"][0].tolist() == P[0].tolist()
+    assert s["unions"][1].tolist() == P[1].tolist()
+    # and so are its per-weighting samples (library Algorithm 1 on the same volumes)
+    for l in range(2):
+        idx, sel = lgk.sample_low_dose(member[l], [N_LD[l]] * K, seed=SEED, level=l)
+        assert idx.tolist() == P[l].tolist()
+        off = (select.shape[0] - len(P[0]) - len(P[1])) + (0 if l == 0 else len(P[0]))
+        np.testing.assert_array_equal(sel, select[off:off + len(P[l])])
+    assert s["case2"].n == phi2.shape[0] + 8 * case.n_iso
+    # second-pass plans against each weighting's own LP (selected points only)
+    st = lgk.fetch_stats(s["res2"])
+    assert st["converged"].all()
+    assert st["rel_pri"].max() <= TOL and st["rel_dual"].max() <= TOL
+    for j in range(K):
+        keep = np.flatnonzero(select[:, j])
+        lr = _lp2(case, phi2[keep], kind2[keep], sid2[keep])
+        br, _, ur = L.bounds(lr, W[j:j + 1])
+        opt = SX.simplex(lr.A, br[:, 0], lr.c, ur[:, 0])
+        assert opt.status == "optimal"
+        gap = abs(st["obj"][j] - opt.obj) / max(1.0, abs(opt.obj))
+        assert gap <= 1e-3, (j, gap)
+    t, _ = lgk.fetch_times(s["res2"])
+    assert np.all(t >= 0)
+
+
+@pytest.mark.parametrize("prec", [0, 2], ids=["fp32", "bf16x3"])
+def test_masked_one_iteration_from_common_state(lgk, setup, prec):
+    s = setup
+    case, W = s["case"], s["W"]
+    member, _ = lgk.low_dose_volumes(s["res1"], s["phi_cand"], (case.d_ld1, case.d_ld2), DELTA)
+    _, phi2, kind2, sid2, select = _pass2_points(s, member)
+    lp = _lp2(case, phi2, kind2, sid2)
+    b, l, u = L.bounds(lp, W, select)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    cs = lgk.create_case(phi2, kind2, sid2, case.n_iso, case.d_presc, case.q_area, case.q_vol,
+                         case.d_ld1, case.d_ld2, case.phi_cal,
+                         params=lgk.default_params(precision=prec))
+    if prec == 0:
+        A = lp.A.astype(np.float32).astype(np.float64)
+        uround = 2.0 ** -24 * np.sqrt(A.shape[1])
+    else:
+        hi = L.bf16_round(lp.A)
+        A = hi + L.bf16_round(lp.A - hi)
+        uround = 2.0 ** -17
+    tol = np.linalg.norm(A, 2) ** 2 * uround
+    for k in (0, 40):
+        ok = AD.admm(A, lp.c, b, l, u, rho, max_iter=k)
+        q1, q2 = (ok.z1 + ok.y1).T, (ok.z2 + ok.y2).T
+        res = lgk.solve_weightings_masked(cs, W, rho, select=select, q1_init=q1, q2_init=q2, tol=0.0,
+                                          max_iter=1)
+        g1, g2 = lgk.fetch_state(res)
+        o = AD.admm(A, lp.c, b, l, u, rho, max_iter=1, state=(ok.z1, ok.z2, ok.y1, ok.y2))
+        r1, r2 = o.z1 + o.y1, o.z2 + o.y2
+        assert np.abs(g1.T - r1).max() <= tol * np.abs(r1).max(), k
+        assert np.abs(g2.T - r2).max() <= tol * np.abs(r2).max(), k
+        # the device objective c^T z1 projects with the masked bounds
+        obj = lgk.fetch_stats(res)["obj"]
+        want = lp.c @ np.clip(g1.T, 0.0, u)
+        scale = (np.abs(lp.c) @ np.clip(g1.T, 0.0, u)).max()
+        assert np.abs(obj - want).max() <= 1e-6 * scale, k
