@@ -37,6 +37,11 @@ WORKLOADS = {"cfg0": 0, "cfg1": 1, "cfg2": 2, "cfg3": 3}
 METRIC = "converged plans/s (81 & 441 weightings) vs plain FP32 form; p50/p99 latency"
 PAPER_ITERS = 3000          # fixed iterations per pass in the paper (Sec. 3.D)
 RHO0_PER_BETA = 1.1e3       # Eq. rho_rule constant per unit of beta (re-tuned, Sec. 3.C)
+PRECISIONS = {"bf16": 1, "bf16x3": 2}     # lgk PREC_* of the BF16 forms
+PRECISION_NOTE = {
+    "bf16": "A as 1 bf16 term (solves the LP of the rounded A), iterates 2 bf16 terms",
+    "bf16x3": ("A as 2 bf16 terms, iterates 2 bf16 terms (3 products per GEMM); S^-1 and solve "
+               "input 3 bf16 terms (6 products); fp32 accumulate")}
 
 
 def peaks():
@@ -49,22 +54,37 @@ def peaks():
         return 6400.0, 1800.0, 1400.0, "fallback"
 
 
-def kernel_work(name, m, n, K, terms=3):
-    """(algorithmic bytes, algorithmic flops, executed tensor flops) of one
-    launch of an iteration kernel.  The BF16X3 GEMMs execute `terms` = 3
-    BF16 products per algorithmic product (A and the iterates as two BF16
-    terms each), the solve 6 (three terms each)."""
-    if name == "gemm1":      # A . R1 (A as 2 bf16 terms once, R1 hi/lo), partial slots out
-        return 4 * m * n + 4 * n * K + 4 * m * K, 2 * m * n * K, terms * 2 * m * n * K
-    if name == "solve":      # S^{-1} . rhs (3 bf16 parts each), partial slots out
-        return 6 * m * m + 6 * m * K + 4 * m * K, 2 * m * m * K, 6 * 2 * m * m * K
-    if name == "gemm2":      # A^T . V + q1 update: A (2 terms) once, V hi/lo, q1 r/w, R1 out
-        return 4 * m * n + 4 * m * K + 12 * n * K, 2 * m * n * K, terms * 2 * m * n * K
+# bytes per entry of A each GEMM streams, per precision form
+A_BYTES = {"bf16": 2, "bf16x3": 4}
+# BF16 products per algorithmic product in the two A GEMMs, per form
+GEMM_TERMS = {"bf16": 2, "bf16x3": 3}
+
+
+def kernel_work(name, m, n, K, form="bf16x3"):
+    """Work of one launch of an iteration kernel: (algorithmic bytes,
+    algorithmic flops, executed tensor flops, executed bytes).
+
+    Algorithmic = the per-unit figures of the method with A and the iterates
+    entering the GEMMs as one BF16 term each (A read once per GEMM: 2mn
+    bytes; iterates 2 bytes, FP32 state 4 bytes; the solve's operator as one
+    FP32 m x m matrix).  Executed = what the chosen form moves and multiplies:
+    A as 2 BF16 terms (4 bytes per entry) or 1 (2 bytes), the iterates as two
+    BF16 terms, S^{-1} and the solve input as three."""
+    a_exec, t = A_BYTES[form], GEMM_TERMS[form]
+    if name == "gemm1":      # A . R1 -> rhs (partial slots)
+        return (2 * m * n + 2 * n * K + 4 * m * K, 2 * m * n * K, t * 2 * m * n * K,
+                a_exec * m * n + 4 * n * K + 4 * m * K)
+    if name == "solve":      # S^{-1} . rhs -> v (partial slots)
+        return (4 * m * m + 4 * m * K + 4 * m * K, 2 * m * m * K, 6 * 2 * m * m * K,
+                6 * m * m + 6 * m * K + 4 * m * K)
+    if name == "gemm2":      # A^T . V, q1 read / write, R1 out
+        return (2 * m * n + 2 * m * K + 10 * n * K, 2 * m * n * K, t * 2 * m * n * K,
+                a_exec * m * n + 4 * m * K + 12 * n * K)
     if name in ("reduce_rhs", "reduce_solve"):
-        return 16 * m * K, 0, 0
+        return 16 * m * K, 0, 0, 16 * m * K
     if name == "q1_update":  # partial sums in, q1 r/w, R1 hi/lo out
-        return 16 * n * K, 0, 0
-    return 0, 0, 0
+        return 16 * n * K, 0, 0, 16 * n * K
+    return 0, 0, 0, 0
 
 
 class Clocks:
@@ -228,10 +248,9 @@ def workload_config(case, W, args):
     m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
     return {"workload": f"{case.name} (A {m}x{n}, K={W.shape[0]} weightings, tol {args.tol:g})",
             "m": m, "n": n, "K": int(W.shape[0]), "tol": args.tol,
-            "precision": ("bf16x3: A as 2 bf16 terms, iterates 2 bf16 terms (3 products per GEMM); "
-                          "S^-1 and solve input 3 bf16 terms (6 products); fp32 accumulate"),
+            "precision": PRECISION_NOTE[args.precision],
             "rho": "Eq. rho_rule, rho0 = 1100 beta", "l2": "inputs larger than L2 (A resident, "
-            f"{4 * m * n / 1e6:.0f} MB as 2 bf16 terms > 126 MB)", "parallelism": "replicas"}
+            f"{A_BYTES[args.precision] * m * n / 1e6:.0f} MB > 126 MB)", "parallelism": "replicas"}
 
 
 def kernel_hash():
@@ -266,7 +285,8 @@ def run_ours(args, rank, world, local):
     cfg = WORKLOADS[args.workload]
     case, W = make_inputs(cfg)
     K = W.shape[0]
-    params = lgk.default_params(precision=lgk.PREC_BF16X3, device=local, profile=1)
+    prec = PRECISIONS[args.precision]
+    params = lgk.default_params(precision=prec, device=local, profile=1)
     from synth import cases as SC
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
@@ -287,6 +307,7 @@ def run_ours(args, rank, world, local):
     lat = []
     ev0.record()
     t_host0 = time.perf_counter()
+    r_last = None
     for _ in range(args.steps):
         t1 = time.perf_counter()
         r = lgk.solve_weightings(cs, W, None, **rule)
@@ -297,7 +318,9 @@ def run_ours(args, rank, world, local):
         for k, (ms, nl) in lgk.fetch_profile(r).items():
             prof[k][0] += ms
             prof[k][1] += nl
-        r.close()
+        if r_last is not None:
+            r_last.close()
+        r_last = r
     ev1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -322,7 +345,7 @@ def run_ours(args, rank, world, local):
     for _ in range(e2e_steps):
         c2 = lgk.create_case(phi_pinned, case.kind, case.struct_id, case.n_iso, case.d_presc,
                              case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
-                             params=lgk.default_params(precision=lgk.PREC_BF16X3, device=local))
+                             params=lgk.default_params(precision=prec, device=local))
         r = lgk.solve_weightings(c2, W, None, **rule)
         t, tau = lgk.fetch_times(r)
         conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
@@ -352,15 +375,15 @@ def run_ours(args, rank, world, local):
             fp32 = {"value": float(s3["converged"].sum()) / dt, "unit": "plans/s",
                     "mean_iters": float(s3["iters"].mean()),
                     "all_converged": bool(s3["converged"].all()),
-                    "ratio_bf16x2_over_fp32": (value / world) / (float(s3["converged"].sum()) / dt)}
+                    "ratio_over_fp32": (value / world) / (float(s3["converged"].sum()) / dt)}
             r.close()
             c3.close()
         hbm, tf_burst, tf_sus, src = peaks()
         m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
         dom = max(prof, key=lambda k: prof[k][0])
         ms_avg = prof[dom][0] / max(prof[dom][1], 1)
-        nbytes, flops, executed = kernel_work(dom, m, n, K)
-        t_hbm = nbytes / (hbm * 1e9)
+        nbytes, flops, executed, xbytes = kernel_work(dom, m, n, K, args.precision)
+        t_hbm = xbytes / (hbm * 1e9)
         t_tensor = executed / (tf_sus * 1e12)
         if t_hbm >= t_tensor:
             achieved = nbytes / (ms_avg / 1e3) / 1e9
@@ -372,7 +395,8 @@ def run_ours(args, rank, world, local):
                              f"{executed / flops:.0f} BF16 products per algorithmic one")}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["executed_tensor_frac"] = executed / (ms_avg / 1e3) / (tf_sus * 1e12)
-        roof["hbm_frac"] = nbytes / (ms_avg / 1e3) / (hbm * 1e9)
+        roof["executed_bytes_per_launch"] = xbytes
+        roof["executed_hbm_frac"] = xbytes / (ms_avg / 1e3) / (hbm * 1e9)
         roof["traffic"] = committed_traffic(dom, args.workload)
         roof["kernel"] = dom
         roof["peak_source"] = (f"{src} (MEASURED_PEAKS.json; hbm_gbs, bf16_tflops_sustained)"
@@ -385,6 +409,9 @@ def run_ours(args, rank, world, local):
         cpu = None
         if not args.no_cpu_baseline:
             cpu = oracle_sample(case, W, mean_iters)
+        extra = {} if args.no_extras else {
+            "plan_metrics": bench_metrics(lgk, case, r_last),
+            "two_pass": bench_two_pass(lgk, case, W, args, local)}
         lat_ms = sorted(x * 1e3 for x in lat)
         out = {"metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -399,10 +426,86 @@ def run_ours(args, rank, world, local):
                "latency_ms": {"p50": lat_ms[len(lat_ms) // 2],
                               "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
                "mean_iters_per_plan": mean_iters, "converged_fraction": conv / (K * args.steps),
-               "fp32_form": fp32}
+               "fp32_form": fp32, **extra}
         print(json.dumps(out), flush=True)
+    r_last.close()
     cs.close()
     return 0
+
+
+def bench_metrics(lgk, case, res, reps=3):
+    """Clinical metrics of all K plans on the device (lgk_fetch_metrics) on a
+    2 mm evaluation grid over the targets' bounding box + 12 mm."""
+    from synth import cases as SC
+    pts, label, _ = SC.eval_grid(case, spacing=2.0, margin=12.0)
+    phi_eval = SC.dose_rate(pts, case.iso)
+    lgk.fetch_metrics(res, phi_eval, label)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        met = lgk.fetch_metrics(res, phi_eval, label)
+    dt = (time.perf_counter() - t0) / reps
+    K, E, B = res.K, phi_eval.shape[0], phi_eval.shape[1]
+    return {"ms_per_call": dt * 1e3, "ms_per_plan": dt * 1e3 / K, "n_eval": int(E), "K": int(K),
+            "dose_fp64_gflops": 2.0 * K * E * B / dt / 1e9,
+            "h2d_bytes": int(phi_eval.nbytes + label.nbytes),
+            "coverage_range": [float(met["coverage"].min()), float(met["coverage"].max())],
+            "bot_range": [float(met["bot"].min()), float(met["bot"].max())],
+            "note": "FP64 doses phi_eval t (dominant), integer threshold counts, BOT; host phi_eval "
+                    "uploaded inside each call"}
+
+
+def bench_two_pass(lgk, case, W, args, local, reps=2, n_ld=1000, delta=(1.0, 0.5), seed=7):
+    """Both passes of the two-pass optimisation (Sec. 2.C) through
+    lgk_two_pass: pass-1 case + solve, low-dose volumes of all plans on the
+    candidates (2 mm grid over the targets' box + 25 mm, outside the targets),
+    Algorithm 1 (n_ld points per weighting and level), pass-2 case + masked
+    solve.  Plus one run through the separate entry points for a breakdown."""
+    from synth import cases as SC
+    pts, label, _ = SC.eval_grid(case, spacing=2.0, margin=25.0)
+    phi_cand = SC.dose_rate(pts[label < 0], case.iso)
+    params = lgk.default_params(precision=PRECISIONS[args.precision], device=local)
+    kw = dict(phi_cand=phi_cand, delta_ld1=delta[0], delta_ld2=delta[1], n_ld1=n_ld, n_ld2=n_ld,
+              seed=seed, w0_bot=SC.W0_BOT, rho0_per_beta=RHO0_PER_BETA, tol=args.tol,
+              max_iter=args.max_iter, params=params)
+    args_case = (case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                 case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, W)
+
+    def once():
+        r1, c2, r2, un = lgk.two_pass(*args_case, **kw)
+        st = lgk.fetch_stats(r2)
+        out = (int(st["converged"].sum()), int(st["iters"].max()), c2.n, [len(u) for u in un])
+        r1.close(), r2.close(), c2.close()
+        return out
+
+    once()
+    t0 = time.perf_counter()
+    runs = [once() for _ in range(reps)]
+    dt = (time.perf_counter() - t0) / reps
+    conv = sum(r[0] for r in runs) / reps
+    # breakdown through the separate entry points
+    K = W.shape[0]
+    tb = {}
+    t = time.perf_counter()
+    c1 = lgk.create_case(*args_case[:10], params=params)
+    tb["setup1_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    r1 = lgk.solve_weightings(c1, W, None, w0_bot=SC.W0_BOT, rho0=RHO0_PER_BETA * c1.beta,
+                              tol=args.tol, max_iter=args.max_iter)
+    tb["solve1_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    member, count = lgk.low_dose_volumes(r1, phi_cand, (case.d_ld1, case.d_ld2), delta)
+    tb["volumes_s"] = time.perf_counter() - t
+    t = time.perf_counter()
+    for l in range(2):
+        lgk.sample_low_dose(member[l], [n_ld] * K, seed=seed, level=l)
+    tb["sampling_s"] = time.perf_counter() - t
+    r1.close(), c1.close()
+    return {"value": conv / dt, "unit": "converged second-pass plans/s", "s_per_call": dt,
+            "converged": conv, "K": K, "max_iters_pass2": runs[-1][1], "n_pass2": runs[-1][2],
+            "union_points": runs[-1][3], "n_cand": int(phi_cand.shape[0]),
+            "volume_sizes": [int(count.min()), int(count.max())], "breakdown": tb,
+            "note": "end to end from host phi and candidates (both cases set up inside the call); "
+                    "pass-2 case set-up and solve are the remainder of s_per_call"}
 
 
 def serve_cases(n_req, seed=4000):
@@ -513,6 +616,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS),
+                    help="BF16 form of A: bf16x3 (two BF16 terms; the plans match FP64), bf16 (one term)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the device plan-metrics and two-pass measurements")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of requests of a Poisson stream")
     ap.add_argument("--serve-workers", type=int, default=2)

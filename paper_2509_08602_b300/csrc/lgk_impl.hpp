@@ -127,7 +127,7 @@ int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
           double* C, int ldc);
 
 // Tensor-core GEMMs (tc_gemm.cu)
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile);
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first);
 int sm_count();
 struct IterCtx;
 IterCtx make_ctx_public(ResultData& r);

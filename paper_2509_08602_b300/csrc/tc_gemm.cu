@@ -3,7 +3,8 @@
 // swizzle, no multicast) through an mbarrier ring, warp-specialised CTA:
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocator + MMA issuer (one elected lane)
-//   warps 2..5  epilogue: tcgen05.ld of the 128 x N accumulator, one row per thread
+//   warps 2..9  epilogue: tcgen05.ld of the 128 x N accumulator, two warps per
+//               TMEM lane quarter (one row per thread, half the columns each)
 //
 // Output tile: 128 rows of the long dimension (m for GEMM1 and the solve, n
 // for GEMM2) x N columns (weightings, N <= 256).  The kernel is persistent and
@@ -85,6 +86,29 @@ __device__ inline void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, 
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
+}
+
+// The same load with an L2 cache policy (createpolicy) attached.
+__device__ inline void tma_load_3d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                        uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "l"(policy)
+        : "memory");
+}
+
+// L2 policy for data read once per launch (the streamed A terms): its lines
+// go first, so the operands reused across tiles and kernels stay in L2.
+__device__ inline uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Asynchronous L2 prefetch of `bytes` (multiple of 16) at a 16-byte aligned address.
+__device__ inline void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -373,6 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
         int it = 0;
+        // A streams through once per launch; the B operand, S^{-1} and the
+        // epilogue's state should outlive it in L2
+        const uint64_t pol_a = policy_evict_first();
         for (int sg = s0; sg < s1 && ok; ++sg) {
             const int* g = a.seg + 5 * sg;
             const int row0 = g[0] * 128, col0 = g[1] * a.n_tile;
@@ -381,6 +408,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
                 ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
                 if (!ok) break;
+                if (EPI == EPI_Q1 && kb == max(g[2], g[3] - 8)) {
+                    // the q1 rows this segment's epilogue reads: into L2 a few
+                    // stages before the accumulator completes (512 B per column)
+                    for (int j = 0; j < a.n_tile; ++j)
+                        prefetch_l2(cx.q1 + (size_t)(col0 + j) * cx.n_pad + row0, 512u);
+                }
                 const uint32_t full = smem_u32(&bars[s]);
                 const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
                 mbar_expect_tx(full, (uint32_t)a.stage_bytes);
@@ -388,12 +421,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (A_MN) {
 #pragma unroll
                     for (int p = 0; p < NA; ++p) {
-                        tma_load_3d(st + p * kABytes, &tmA, row0, kx, p, full);
-                        tma_load_3d(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full);
+                        tma_load_3d_hint(st + p * kABytes, &tmA, row0, kx, p, full, pol_a);
+                        tma_load_3d_hint(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full, pol_a);
                     }
-                } else {
+                } else if (EPI == EPI_PARTIAL && NT == 6) {
+                    // the solve: S^{-1} is re-read every iteration, keep its policy
 #pragma unroll
                     for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, &tmA, kx, row0, p, full);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < NA; ++p)
+                        tma_load_3d_hint(st + p * kABytes, &tmA, kx, row0, p, full, pol_a);
                 }
                 const uint32_t sb = st + NA * kABytes;
 #pragma unroll
@@ -579,25 +617,38 @@ int sm_count() {
 // Stream-K plan: the units (column tile, row tile, k block), in that order,
 // cut into `grid` contiguous runs of equal length (+-1), each run split into
 // segments at tile boundaries.  Depends only on the GEMM's shape.
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile) {
-    const long long U = (long long)rows * col_tiles * kb_total;
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first) {
+    const long long T = (long long)rows * col_tiles;
+    const long long U = T * kb_total;
     const int grid = (int)std::min<long long>(sm_count(), U);
     std::vector<int> cta_seg(grid + 1), seg, tile_begin(rows * col_tiles + 1, 0);
     std::vector<std::vector<int>> per_tile(rows * col_tiles);
     int nseg = 0;
+    auto add = [&](long long tile, int kb0, int kb1) {
+        int ct = (int)(tile / rows), rt = (int)(tile % rows);
+        seg.insert(seg.end(), {rt, ct, kb0, kb1, nseg});
+        per_tile[tile].push_back(nseg);
+        ++nseg;
+    };
+    // split_first (a GEMM that finishes its tiles in its own epilogue): every
+    // CTA owns floor(T / grid) whole tiles and the remaining tiles' k blocks
+    // are shared out evenly; each CTA runs its shared pieces first, so the
+    // tiles assembled from several CTAs' partial sums complete early and the
+    // last work of every CTA is a whole tile (no partial sums to gather).
+    const long long full = split_first ? T / grid : 0;
+    const long long t_split0 = full * grid;             // tiles [t_split0, T) are shared
+    const long long Us = (T - t_split0) * kb_total;
     for (int c = 0; c < grid; ++c) {
         cta_seg[c] = nseg;
-        long long u0 = U * c / grid, u1 = U * (c + 1) / grid;
+        long long u0 = t_split0 * kb_total + Us * c / grid, u1 = t_split0 * kb_total + Us * (c + 1) / grid;
         while (u0 < u1) {
             long long tile = u0 / kb_total;
             int kb0 = (int)(u0 % kb_total);
             int kb1 = (int)std::min<long long>(kb_total, kb0 + (u1 - u0));
-            int ct = (int)(tile / rows), rt = (int)(tile % rows);
-            seg.insert(seg.end(), {rt, ct, kb0, kb1, nseg});
-            per_tile[tile].push_back(nseg);
-            ++nseg;
+            add(tile, kb0, kb1);
             u0 += kb1 - kb0;
         }
+        for (long long f = 0; f < full; ++f) add((long long)c * full + f, 0, kb_total);
     }
     cta_seg[grid] = nseg;
     // number the slots tile by tile, in k order, so a tile's partial sums are
@@ -697,9 +748,9 @@ int tc_prepare(ResultData& r) {
     if ((rc = set_smem_attr<2, 2, 3, true, EPI_Q1>())) return rc;
     if ((rc = maps_for(r, r.maps))) return rc;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
-    if ((rc = build_plan(r.plan1, mt, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile))) return rc;
-    if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s))) return rc;
-    if ((rc = build_plan(r.plan2, nt, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile))) return rc;
+    if ((rc = build_plan(r.plan1, mt, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false))) return rc;
+    if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s, false))) return rc;
+    if ((rc = build_plan(r.plan2, nt, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true))) return rc;
     size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile, (size_t)r.plan_s.nseg * r.n_tile_s,
                              (size_t)r.plan2.nseg * r.n_tile});
     return r.part.alloc(slots * 128 * 4);
