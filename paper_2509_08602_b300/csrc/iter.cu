@@ -131,6 +131,8 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
 // rhs = A R1 + q2 - 2 P2(q2).  Grid (m_pad / 128, Kp), 128 threads.
 template <bool BF16>
 __global__ void __launch_bounds__(128) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
+    pdl_trigger();
+    pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     const int i = blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
     const size_t o = (size_t)j * cx.m_pad + i;
@@ -156,6 +158,8 @@ __global__ void __launch_bounds__(128) k_reduce_rhs(IterCtx cx, SumSrc src, void
 // per 128-row tile and column).  Grid (m_pad / 128, Kp), 128 threads.
 template <bool BF16>
 __global__ void __launch_bounds__(128) k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
+    pdl_trigger();
+    pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     const int rt = blockIdx.x, i = rt * 128 + threadIdx.x, j = blockIdx.y;
     const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
@@ -224,6 +228,8 @@ __global__ void __launch_bounds__(128) k_q1_update(IterCtx cx, SumSrc src, void*
 // deterministic); the last block to finish (ticket) updates the control
 // block.
 __global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
+    pdl_trigger();
+    pdl_wait();
     Control* c = cx.ctrl;
     if (c->n_active == 0) return;
     const int j = blockIdx.x, it = c->iter + 1;
@@ -424,20 +430,23 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     cudaStream_t st = cs.stream;
     int rc;
     dim3 gm(cs.m_pad / 128, r.Kp);
+    // consecutive kernels overlap launch and set-up with the predecessor's
+    // tail (programmatic dependent launch), except across profiling events
+    const bool pdl = r.prof_ev.empty();
     prof_mark(r, itx, 0);
-    if ((rc = tc_gemm1(r))) return rc;
+    if ((rc = tc_gemm1(r, pdl && itx > 0))) return rc;
     prof_mark(r, itx, 1);
-    k_reduce_rhs<true><<<gm, 128, 0, st>>>(cx, plan_src(r, r.plan1), r.rhs.p);
+    LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p));
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
-    if ((rc = tc_solve(r))) return rc;
+    if ((rc = tc_solve(r, pdl))) return rc;
     prof_mark(r, itx, 3);
-    k_reduce_solve<true><<<gm, 128, 0, st>>>(cx, plan_src(r, r.plan_s), r.V.p);
+    LGK_CUDA_TRY(launch_k(k_reduce_solve<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan_s), r.V.p));
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
-    if ((rc = tc_gemm2(r))) return rc;
+    if ((rc = tc_gemm2(r, pdl))) return rc;
     prof_mark(r, itx, 5);
-    k_finalize<<<r.Kp, 128, 0, st>>>(cx);
+    LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 6);
     return LGK_OK;

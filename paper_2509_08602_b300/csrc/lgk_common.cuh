@@ -48,6 +48,33 @@ __host__ __device__ inline long long round_up(long long x, long long r) {
     return (x + r - 1) / r * r;
 }
 
+// Programmatic dependent launch (kernels of one iteration launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization).  pdl_trigger lets the
+// next kernel of the stream start launching (its CTAs run their set-up on SMs
+// this kernel has left); pdl_wait blocks until the previous kernel of the
+// stream has completed and its writes are visible.  Without a programmatic
+// predecessor the wait returns at once.
+__device__ inline void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ inline void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch `kern` on `st`, allowed to overlap the previous kernel's tail when
+// `pdl` (the kernel must call pdl_wait before reading that kernel's output).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Device-side error codes written into Control::err.
 enum DeviceError : int {
     DERR_NONE = 0,

@@ -132,8 +132,8 @@ int sm_count();
 struct IterCtx;
 IterCtx make_ctx_public(ResultData& r);
 int tc_prepare(ResultData& r);  // attributes + TMA maps, before capture
-int tc_gemm1(ResultData& r);     // part[s] = Ahat . R1^T over split s of the columns
-int tc_solve(ResultData& r);     // part[s] = G3 . rhs^T  (5 products)
-int tc_gemm2(ResultData& r);     // fused: q1, R1 update from Ahat^T . V
+int tc_gemm1(ResultData& r, bool pdl = false);     // part[s] = Ahat . R1^T over split s of the columns
+int tc_solve(ResultData& r, bool pdl = false);     // part[s] = G3 . rhs^T  (6 products)
+int tc_gemm2(ResultData& r, bool pdl = false);     // fused: q1, R1 update from Ahat^T . V
 
 }  // namespace lgk

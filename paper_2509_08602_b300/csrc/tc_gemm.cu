@@ -364,8 +364,8 @@ template <int NA, int NB, int NT, bool A_MN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs a, IterCtx cx) {
+    pdl_trigger();
     Control* ctrl = cx.ctrl;
-    if (ctrl->n_active == 0 || ctrl->err) return;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int S = a.stages;
@@ -392,8 +392,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // set-up done; from here on the previous kernel's output is read
+    pdl_wait();
+    const bool run = ctrl->n_active != 0 && ctrl->err == 0;
 
-    if (warp == 0 && lane == 0) {
+    if (!run) {
+        // every column has stopped (or an error is pending): nothing to do
+    } else if (warp == 0 && lane == 0) {
         // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
         int it = 0;
@@ -425,7 +430,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tma_load_3d_hint(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full, pol_a);
                     }
                 } else if (EPI == EPI_PARTIAL && NT == 6) {
-                    // the solve: S^{-1} is re-read every iteration, keep its policy
+                    // the solve: S^{-1} is re-read every iteration, default policy
+                    // (an evict-last hint did not keep its 6 m^2 bytes in L2)
 #pragma unroll
                     for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, &tmA, kx, row0, p, full);
                 } else {
@@ -688,7 +694,7 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, b
 
 template <int NA, int NB, int NT, bool A_MN, int EPI>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
-                  void* out) {
+                  void* out, bool pdl) {
     TcArgs a{};
     a.cta_seg = P.cta_seg;
     a.seg = P.seg;
@@ -709,7 +715,8 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
     a.nbuf = 4 * a.tmem_cols <= 512 ? 4 : 2;
     size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
-    k_tc_gemm<NA, NB, NT, A_MN, EPI><<<P.grid, kThreads, smem, r.cs->stream>>>(mA, mB, a, make_ctx_public(r));
+    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI>, dim3(P.grid), dim3(kThreads), smem, r.cs->stream,
+                          pdl, mA, mB, a, make_ctx_public(r)));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -756,18 +763,19 @@ int tc_prepare(ResultData& r) {
     return r.part.alloc(slots * 128 * 4);
 }
 
-int tc_gemm1(ResultData& r) {
-    if (r.cs->na == 2) return launch<2, 2, 3, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr);
-    return launch<1, 2, 2, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr);
+int tc_gemm1(ResultData& r, bool pdl) {
+    if (r.cs->na == 2)
+        return launch<2, 2, 3, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr, pdl);
+    return launch<1, 2, 2, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr, pdl);
 }
 
-int tc_solve(ResultData& r) {
-    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr);
+int tc_solve(ResultData& r, bool pdl) {
+    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr, pdl);
 }
 
-int tc_gemm2(ResultData& r) {
-    if (r.cs->na == 2) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p);
-    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p);
+int tc_gemm2(ResultData& r, bool pdl) {
+    if (r.cs->na == 2) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
 }
 
 }  // namespace lgk
