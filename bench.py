@@ -385,10 +385,13 @@ def run_ours(args, rank, world, local):
             r = lgk.solve_weightings(c3, W, None, **rule)
             dt = time.perf_counter() - t0
             s3 = lgk.fetch_stats(r)
-            fp32 = {"value": float(s3["converged"].sum()) / dt, "unit": "plans/s",
-                    "mean_iters": float(s3["iters"].mean()),
+            n3 = int(s3["converged"].sum())
+            fp32 = {"value": n3 / dt, "unit": "plans/s", "mean_iters": float(s3["iters"].mean()),
+                    "converged": n3, "K": K, "max_iter": args.max_iter,
                     "all_converged": bool(s3["converged"].all()),
-                    "ratio_over_fp32": (value / world) / (float(s3["converged"].sum()) / dt)}
+                    "ratio_over_fp32": (value / world) / (n3 / dt) if n3 else None,
+                    "median_rel_pri": float(np.median(s3["rel_pri"])),
+                    "median_rel_dual": float(np.median(s3["rel_dual"]))}
             r.close()
             c3.close()
         hbm, tf_burst, tf_sus, src = peaks()
