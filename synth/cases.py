@@ -130,6 +130,7 @@ def _sample(rng, idx: np.ndarray, count: int, xyz_flat: np.ndarray, h: float):
 
 def make_case(targets, *, n_target_pts: int, n_ring: int, n_ld1: int, n_ld2: int,
               n_iso: int, seed: int, name: str = "case", d_presc=None,
+              oars=None, n_oar: int = 0,
               with_phi: bool = True, phi_dtype=np.float64) -> Case:
     """Sample dose points by class (Sec. 2.A) and build the inputs.
 
@@ -139,6 +140,9 @@ def make_case(targets, *, n_target_pts: int, n_ring: int, n_ld1: int, n_ld2: int
     nearest target voxel).  Target points are split between targets and
     between TS/TI by voxel share; ring points between targets by ring-voxel
     share.  Isocenters are distinct target voxels drawn uniformly.
+    oars: optional list of (centre, semi-axes, maximum dose D_O) organs at
+    risk (Appendix A); n_oar points are sampled in each, from its voxels
+    outside the targets, and appended after the other classes.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     targets = [(np.asarray(c, float), np.asarray(a, float)) for c, a in targets]
@@ -190,13 +194,28 @@ def make_case(targets, *, n_target_pts: int, n_ring: int, n_ld1: int, n_ld2: int
 
     tidx = np.flatnonzero(labf >= 0)
     iso = xyz_flat[rng.choice(tidx, size=n_iso, replace=False)].copy()
+    d_oar = np.zeros(0)
+    if oars:
+        o_pts, o_kind, o_sid = [], [], []
+        for o, (c, a, _) in enumerate(oars):
+            c, a = np.asarray(c, float), np.asarray(a, float)
+            idx = np.flatnonzero(((((xyz_flat - c) / a) ** 2).sum(1) <= 1.0) & (labf < 0))
+            if idx.size == 0:
+                raise ValueError(f"OAR {o} has no voxel outside the targets inside the grid")
+            o_pts.append(_sample(rng, idx, n_oar, xyz_flat, h))
+            o_kind.append(np.full(n_oar, KIND_OAR, np.uint8))
+            o_sid.append(np.full(n_oar, o, np.uint16))
+        points = np.ascontiguousarray(np.concatenate([points] + o_pts))
+        kind = np.ascontiguousarray(np.concatenate([kind] + o_kind))
+        struct_id = np.ascontiguousarray(np.concatenate([struct_id] + o_sid))
+        d_oar = np.array([float(d) for _, _, d in oars])
     phi = dose_rate(points, iso, dtype=phi_dtype) if with_phi else None
     if d_presc is None:
         d_presc = np.full(nT, D_PRESC)
     return Case(name=name, n_iso=n_iso, points=points, kind=kind, struct_id=struct_id,
                 iso=iso, phi=phi, d_presc=np.asarray(d_presc, float),
                 q_area=svox / svox.sum(), q_vol=tvox / tvox.sum(),
-                d_oar=np.zeros(0), d_ld1=D_LD1, d_ld2=D_LD2, phi_cal=PHI_CAL,
+                d_oar=d_oar, d_ld1=D_LD1, d_ld2=D_LD2, phi_cal=PHI_CAL,
                 targets=targets, seed=seed)
 
 

@@ -282,3 +282,52 @@ def test_device_metrics_two_targets_unequal_prescriptions(lgk):
     # every evaluation point outside the targets: coverage 0 of 0 target points
     far = lgk.fetch_metrics(res, phi_eval[label < 0][:50], label[label < 0][:50])
     assert np.all(far["coverage"] == 0.0)
+
+
+def test_oar_and_unequal_prescriptions(lgk):
+    """Appendix A's hard organ-at-risk constraints and per-target
+    prescriptions: a two-target case (20 and 16 Gy) with an organ at risk
+    between them whose maximum dose binds.  The device plans reach the
+    simplex optimum, keep the organ within its limit (to the ADMM
+    tolerance), and their metrics follow the FP64 oracle ADMM."""
+    targets = [(np.array([-7.0, 0, 0]), np.full(3, 5.0)), (np.array([8.0, 0, 0]), np.full(3, 4.0))]
+    base = dict(n_target_pts=600, n_ring=300, n_ld1=300, n_ld2=300, n_iso=8, seed=91,
+                d_presc=[20.0, 16.0])
+    organ = ((0.5, 7.0, 0.0), (3.0, 3.0, 3.0))
+    W = SC.slider_weights(2)
+
+    def simplex_plans(case):
+        lp = L.precondition(L.assemble_case(case))
+        b, l, u = L.bounds(lp, W)
+        res = [SX.simplex(lp.A, b[:, j], lp.c, u[:, j]) for j in range(W.shape[0])]
+        oar = case.kind == SC.KIND_OAR
+        t = np.stack([L.times_from_multipliers(lp, r.lam)[0][:, 0] for r in res], 1)
+        return lp, b, l, u, np.array([r.obj for r in res]), (case.phi[oar] @ t).max(0)
+
+    free = SC.make_case(targets, **base, oars=[organ + (1e9,)], n_oar=60)
+    d_o = 0.6 * simplex_plans(free)[5].min()
+    case = SC.make_case(targets, **base, oars=[organ + (d_o,)], n_oar=60)
+    lp, b, l, u, opt, d_simplex = simplex_plans(case)
+    assert np.all(d_simplex <= d_o * (1 + 1e-9)) and np.all(d_simplex >= d_o * (1 - 1e-6))
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                         case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, d_oar=case.d_oar,
+                         params=lgk.default_params(precision=lgk.PREC_BF16X3))
+    res = lgk.solve_weightings(cs, W, rho, tol=TOL, max_iter=30000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
+    assert gap.max() <= 1e-3
+    t, _ = lgk.fetch_times(res)
+    oar_pts = case.phi[case.kind == SC.KIND_OAR]
+    assert np.all((oar_pts @ t.T).max(0) <= d_o * 1.005)
+    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=30000, tol=TOL)
+    t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
+    pts, label, _ = SC.eval_grid(case, spacing=1.0, margin=12.0)
+    phi_eval = SC.dose_rate(pts, case.iso)
+    met = lgk.fetch_metrics(res, phi_eval, label)
+    met_ref = M.plan_metrics(M.dose(phi_eval, t_ref), label, case.d_presc, t_ref, case.n_iso)
+    assert np.all(np.isnan(met["gi"])) and np.all(np.isnan(met_ref["gi"]))
+    for key in ("coverage", "selectivity", "bot"):
+        rel = np.abs(met[key] - met_ref[key]) / np.abs(met_ref[key])
+        assert rel.max() <= 5e-3, (key, rel)
