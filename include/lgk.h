@@ -97,6 +97,14 @@ typedef struct {
     int timeout_ms;          /* bound on any single host wait; default 600000                   */
     int profile;             /* 1: time every kernel of every iteration with CUDA events
                                 (read by lgk_fetch_profile); default 0                       */
+    int lo_refresh;          /* LGK_PREC_BF16X3 only.  1 (default): iterate with the high BF16
+                                term of A and add the low term's product from the last full
+                                iteration (lo R1 and lo^T v, kept in FP32); the first
+                                iteration of every graph replay and every residual-test
+                                iteration use both terms and refresh those products.  The
+                                fixed point, hence every converged plan, is that of the
+                                two-term A; the heavy products read half the bytes.
+                                0: both terms every iteration (the literal iteration).      */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
@@ -335,11 +343,15 @@ int lgk_two_pass(const lgk_case_desc* desc, const lgk_params* p, int K, const do
  * back to lgk_solve_weightings_warm resumes the iteration. */
 int lgk_fetch_state(const lgk_result* res, double* q1, double* q2);
 
-/* Kernel classes of one ADMM iteration, in launch order.  The BF16 forms run
- * the q1 update inside the tensor-core GEMM2's epilogue (LGK_K_Q1_UPDATE
- * reports zero launches for them); the FP32 form launches all seven. */
+/* Kernel classes of one ADMM iteration.  Launch order: [GEMM1_LO] GEMM1
+ * REDUCE_RHS SOLVE REDUCE_SOLVE [GEMM2_LO] GEMM2 [Q1_UPDATE] FINALIZE.  The
+ * BF16 forms run the q1 update inside the tensor-core GEMM2's epilogue
+ * (LGK_K_Q1_UPDATE reports zero launches for them); the FP32 form launches
+ * it.  GEMM1_LO / GEMM2_LO (lo R1 and lo^T v) run on the full iterations of
+ * LGK_PREC_BF16X3 with lo_refresh = 1. */
 enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLVE = 3,
-       LGK_K_GEMM2 = 4, LGK_K_Q1_UPDATE = 5, LGK_K_FINALIZE = 6, LGK_K_COUNT = 7 };
+       LGK_K_GEMM2 = 4, LGK_K_Q1_UPDATE = 5, LGK_K_FINALIZE = 6, LGK_K_GEMM1_LO = 7,
+       LGK_K_GEMM2_LO = 8, LGK_K_COUNT = 9 };
 
 /* Per-kernel-class device time of a solve made with lgk_params.profile = 1:
  * ms[LGK_K_COUNT] total milliseconds between CUDA events recorded on the

@@ -27,6 +27,17 @@ r = x' - z' and s = rho (z' - z), column j stops once
     ||r|| <= eps_abs sqrt(n+m) + tol max(||x'||, ||z'||)   and
     ||s|| <= eps_abs sqrt(n+m) + tol ||rho y'||,
 checked every `check_every` iterations; a stopped column keeps its iterate.
+
+Lagged low term (`lagged_lo`, the device's default iteration for the
+two-term BF16 form; not in the paper): with A = A_hi + E, the two products
+of an iteration use A_hi and add E applied to the operands of the last
+"full" iteration, r1_f and v_f:
+    A r1   ~  A_hi r1 + E r1_f,        A^T v  ~  A_hi^T v + E^T v_f.
+Full iterations use A itself and refresh r1_f, v_f: the first one and every
+`refresh`-th (the residual-test iterations, k + 1 = 0 mod refresh); `restart`
+(0 for none) adds the iterations k = 0 mod restart.  A fixed point of this
+iteration has r1 = r1_f, v = v_f, hence is a fixed point of the literal
+iteration with A.
 """
 from __future__ import annotations
 
@@ -61,12 +72,15 @@ class AdmmResult:
 
 
 def admm(A, c, b, l, u, rho, *, max_iter: int, tol: float | None = None,
-         check_every: int = 10, eps_abs: float = 1e-12, state=None) -> AdmmResult:
+         check_every: int = 10, eps_abs: float = 1e-12, state=None,
+         lagged_lo=None) -> AdmmResult:
     """Run the literal ADMM iteration above for all K columns.
 
     A (m, n); c (n,); b (m, K); l, u (n, K); rho (K,).  With tol=None every
     column runs exactly `max_iter` iterations.  `state` optionally gives
     (z1, z2, y1, y2) to start from (default zeros, as the paper is silent).
+    `lagged_lo` = (A_hi, refresh, restart) runs the lagged-low-term variant
+    described in the module docstring (S is formed from A in both cases).
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -87,13 +101,30 @@ def admm(A, c, b, l, u, rho, *, max_iter: int, tol: float | None = None,
     rel_pri = np.full(K, np.inf)
     rel_dual = np.full(K, np.inf)
     sq = np.sqrt(n + m)
+    if lagged_lo is not None:
+        A_hi, refresh, restart = lagged_lo
+        A_hi = np.asarray(A_hi, dtype=np.float64)
+        E = A - A_hi
+        r1_f, v_f = np.zeros((n, K)), np.zeros((m, K))
     for k in range(max_iter):
         if not active.any():
             break
         a = np.flatnonzero(active)
         r1 = z1[:, a] - y1[:, a] - c_over_rho[:, a]
-        v = scipy.linalg.cho_solve(cf, A @ r1 - z2[:, a] + y2[:, a])
-        nx1 = r1 - A.T @ v
+        full = (lagged_lo is None or k == 0 or (k + 1) % refresh == 0
+                or (restart > 0 and k % restart == 0))
+        if full:
+            Ar1 = A @ r1
+        else:
+            Ar1 = A_hi @ r1 + E @ r1_f[:, a]
+        v = scipy.linalg.cho_solve(cf, Ar1 - z2[:, a] + y2[:, a])
+        if full:
+            ATv = A.T @ v
+            if lagged_lo is not None:
+                r1_f[:, a], v_f[:, a] = r1, v
+        else:
+            ATv = A_hi.T @ v + E.T @ v_f[:, a]
+        nx1 = r1 - ATv
         nx2 = v + z2[:, a] - y2[:, a]
         nz1 = np.clip(nx1 + y1[:, a], l[:, a], u[:, a])
         nz2 = np.minimum(nx2 + y2[:, a], b[:, a])

@@ -56,6 +56,7 @@ struct SumSrc {
     const int* tile_begin;
     const int* tile_slots;
     int rows_pad, row_tiles, n_tile;
+    int mt;                 // 128-row sub-tiles per tile: slots are [slot][mt][n_tile][128]
 };
 
 // Sum of the GEMM output at (i, j): the plain matrix, or the tile's slots.
@@ -63,10 +64,10 @@ struct SumSrc {
 // loads of the different slots are independent of each other.
 __device__ inline float gemm_out(const SumSrc& s, int i, int j) {
     if (!s.tile_begin) return s.part[(size_t)j * s.rows_pad + i];
-    const int ct = j / s.n_tile, t = ct * s.row_tiles + (i >> 7);
+    const int ct = j / s.n_tile, t = ct * s.row_tiles + (i >> 7) / s.mt, h = (i >> 7) % s.mt;
     const int b = __ldg(s.tile_begin + t), e = __ldg(s.tile_begin + t + 1);
-    const float* p = s.part + ((size_t)b * s.n_tile + (j - ct * s.n_tile)) * 128 + (i & 127);
-    const size_t stride = (size_t)s.n_tile * 128;
+    const float* p = s.part + (((size_t)b * s.mt + h) * s.n_tile + (j - ct * s.n_tile)) * 128 + (i & 127);
+    const size_t stride = (size_t)s.mt * s.n_tile * 128;
     float acc = 0.f;
     int k = 0;
     for (; k + 4 <= e - b; k += 4) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(128) k_reduce_rhs(IterCtx cx, SumSrc src, void
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     const int i = blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
     const size_t o = (size_t)j * cx.m_pad + i;
-    const float acc = gemm_out(src, i, j);
+    const float acc = gemm_out(src, i, j) + (cx.c1 ? cx.c1[o] : 0.f);
     const float q = cx.q2[o];
     const float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
     const float r = acc + q - 2.f * p2;
@@ -348,6 +349,8 @@ static IterCtx make_ctx(ResultData& r) {
     cx.col_slot = cs.col_slot.as<uint8_t>();
     cx.utab = r.utab.as<float>();
     cx.mask = r.mask_words ? r.mask.as<uint32_t>() : nullptr;
+    cx.c1 = r.refine ? r.c1.as<float>() : nullptr;
+    cx.c2 = r.refine ? r.c2.as<float>() : nullptr;
     cx.mask_words = r.mask_words;
     cx.c_slot = r.utab.as<float>() + (size_t)r.Kp * cs.n_slot;
     cx.rho = r.colp.as<float>();
@@ -367,10 +370,10 @@ static IterCtx make_ctx(ResultData& r) {
 
 IterCtx make_ctx_public(ResultData& r) { return make_ctx(r); }
 
-static SumSrc plain_src(const float* p, int rows_pad) { return SumSrc{p, nullptr, nullptr, rows_pad, 0, 1}; }
+static SumSrc plain_src(const float* p, int rows_pad) { return SumSrc{p, nullptr, nullptr, rows_pad, 0, 1, 1}; }
 
 static SumSrc plan_src(const ResultData& r, const GemmPlan& P) {
-    return SumSrc{r.part.as<float>(), P.tile_begin, P.tile_slots, 0, P.rows, P.n_tile};
+    return SumSrc{r.part.as<float>(), P.tile_begin, P.tile_slots, 0, P.rows, P.n_tile, P.mt};
 }
 
 static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
@@ -433,22 +436,39 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     // consecutive kernels overlap launch and set-up with the predecessor's
     // tail (programmatic dependent launch), except across profiling events
     const bool pdl = r.prof_ev.empty();
+    // lo_refresh: the low term's products are recomputed on the solve's
+    // first iteration and on every residual-test iteration, so each test sees
+    // the two-term operator; in between they are reused.  The graph's first
+    // slot carries the first iteration's refresh, skipped on the device in
+    // later replays.
+    const bool test_slot = (itx + 1) % cs.prm.check_every == 0;
+    const bool full = r.refine && (itx == 0 || test_slot);
+    const bool first_only = itx == 0 && !test_slot;
+    auto ran = [&](int k, bool v) {
+        if (!r.prof_ran.empty()) r.prof_ran[(size_t)itx * r.prof_class.size() + k] = v;
+    };
     prof_mark(r, itx, 0);
-    if ((rc = tc_gemm1(r, pdl && itx > 0))) return rc;
+    if (full && (rc = tc_gemm1_lo(r, pdl && itx > 0, first_only))) return rc;
+    ran(0, full);
     prof_mark(r, itx, 1);
+    if ((rc = tc_gemm1(r, pdl && (itx > 0 || full)))) return rc;
+    prof_mark(r, itx, 2);
     LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p));
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 2);
-    if ((rc = tc_solve(r, pdl))) return rc;
     prof_mark(r, itx, 3);
+    if ((rc = tc_solve(r, pdl))) return rc;
+    prof_mark(r, itx, 4);
     LGK_CUDA_TRY(launch_k(k_reduce_solve<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan_s), r.V.p));
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 4);
-    if ((rc = tc_gemm2(r, pdl))) return rc;
     prof_mark(r, itx, 5);
+    if (full && (rc = tc_gemm2_lo(r, pdl, first_only))) return rc;
+    ran(5, full);
+    prof_mark(r, itx, 6);
+    if ((rc = tc_gemm2(r, pdl))) return rc;
+    prof_mark(r, itx, 7);
     LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 6);
+    prof_mark(r, itx, 8);
     return LGK_OK;
 }
 
@@ -520,6 +540,12 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if (!bf16 && (rc = r.W.alloc(nq * 4))) return rc;
     if (!bf16 && (rc = r.part.alloc(mq * 4))) return rc;     // BF16 forms: tc_prepare
     if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
+    r.refine = cs.na == 2 && cs.prm.lo_refresh;
+    if (r.refine) {
+        if ((rc = r.c1.alloc(mq * 4)) || (rc = r.c2.alloc(nq * 4))) return rc;
+        LGK_CUDA_TRY(cudaMemsetAsync(r.c1.p, 0, r.c1.bytes, st));
+        LGK_CUDA_TRY(cudaMemsetAsync(r.c2.p, 0, r.c2.bytes, st));
+    }
     if (mask && (rc = r.mask.alloc(mdev.size() * 4))) return rc;
     if ((rc = r.active.alloc((size_t)2 * Kp * 4)) || (rc = r.iters.alloc((size_t)Kp * 4))) return rc;
     if ((rc = r.ctrl.alloc(sizeof(Control)))) return rc;
@@ -576,8 +602,8 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     cudaGraph_t g = nullptr;
     // kernel classes of one iteration, in launch order
     if (bf16)
-        r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE, LGK_K_GEMM2,
-                        LGK_K_FINALIZE};
+        r.prof_class = {LGK_K_GEMM1_LO, LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
+                        LGK_K_GEMM2_LO, LGK_K_GEMM2, LGK_K_FINALIZE};
     else
         r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
                         LGK_K_GEMM2, LGK_K_Q1_UPDATE, LGK_K_FINALIZE};
@@ -585,10 +611,9 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if (cs.prm.profile) {
         r.prof_ev.assign((size_t)per_graph * (kpi + 1), nullptr);
         for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
+        r.prof_ran.assign((size_t)per_graph * kpi, 1);
     }
     LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    long long before = 0;
-    (void)before;
     for (int it = 0; it < per_graph; ++it) {
         rc = bf16 ? iteration_bf16(r, cx, it) : iteration_fp32(r, cx, it);
         if (rc) {
@@ -598,6 +623,18 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         }
     }
     LGK_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    // kernels per replay: the graph's kernel nodes (the captured launches
+    // were counted at capture time, when nothing ran)
+    size_t n_nodes = 0, n_all = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n_all) == cudaSuccess && n_all) {
+        std::vector<cudaGraphNode_t> nodes(n_all);
+        if (cudaGraphGetNodes(g, nodes.data(), &n_all) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
+            }
+    }
+    count_launch(-(long long)n_nodes);
     cudaError_t e = cudaGraphInstantiate(&r.graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -605,10 +642,6 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         return LGK_ECUDA;
     }
     r.graph_iters = per_graph;
-    size_t n_nodes = 0;
-    {
-        n_nodes = (size_t)per_graph * kpi;
-    }
 
     Control* hc = nullptr;
     LGK_CUDA_TRY(cudaMallocHost(&hc, sizeof(Control)));
@@ -644,6 +677,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
                 for (size_t k = 0; k < kpi; ++k) {
                     float ms = 0.f;
                     const size_t e0 = (size_t)it * (kpi + 1) + k;
+                    if (!r.prof_ran[(size_t)it * kpi + k]) continue;      // slot without a kernel
                     if (cudaEventElapsedTime(&ms, r.prof_ev[e0], r.prof_ev[e0 + 1]) == cudaSuccess) {
                         r.prof_ms[r.prof_class[k]] += ms;
                         r.prof_n[r.prof_class[k]] += 1;

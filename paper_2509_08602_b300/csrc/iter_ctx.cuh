@@ -12,6 +12,8 @@ struct IterCtx {
     const uint8_t* col_slot;
     const float* utab;      // [Kp][n_slot]
     const uint32_t* mask;   // [n_pad][mask_words] point selection per column, or NULL (all)
+    const float* c1;        // lo_refresh: [Kp][m_pad] lo R1 of the last full iteration, or NULL
+    const float* c2;        // lo_refresh: [Kp][n_pad] lo^T v of the last full iteration, or NULL
     int mask_words;
     const float* c_slot;    // [n_slot] (stored after utab)
     const float* rho;       // colp[0]

@@ -58,6 +58,7 @@ struct TcMaps {
     CUtensorMap A_mn;   // A terms, tiles 64 rows x 64 columns read MN-major (GEMM2)
     CUtensorMap G3;     // S^{-1} hi/mid/lo, 128 x 64 tiles (solve)
     CUtensorMap R1, rhs, V;   // hi/lo iterates, n_tile x 64 tiles
+    CUtensorMap Alo_k, Alo_mn;   // A's low BF16 term alone (lo_refresh products)
 };
 
 // Stream-K work plan of one tensor-core GEMM (device int arrays, see
@@ -66,6 +67,7 @@ struct TcMaps {
 struct GemmPlan {
     DevBuf buf;
     int grid = 0, nseg = 0, rows = 0, col_tiles = 0, n_tile = 0;
+    int mt = 1;                     // 128-row sub-tiles per output tile (tile height 128 mt)
     const int* cta_seg = nullptr;
     const int* seg = nullptr;
     const int* tile_begin = nullptr;
@@ -88,6 +90,9 @@ struct ResultData {
     DevBuf part;              // float segment partial sums [slot][n_tile][128] (BF16 forms), or
                               // one GEMM output [Kp][rows] (FP32 form)
     DevBuf utab;              // float [Kp][n_slot] upper bounds u per slot
+    bool refine = false;      // lo_refresh: heavy products with A_hi, lo products lagged
+    bool wide = false;        // GEMM1 / GEMM2 (and the lo products) on 256-row tiles
+    DevBuf c1, c2;            // float [Kp][m_pad] lo R1_hi, [Kp][n_pad] lo^T V_hi (last full iteration)
     DevBuf mask;              // uint32 [n_pad][mask_words] point selection, when given
     int mask_words = 0;       // 0: every point in every column
     DevBuf colp;              // float [4][Kp]: rho, 1/rho, w_BOT, unused
@@ -101,6 +106,7 @@ struct ResultData {
     int graph_iters = 0;
     std::vector<int> prof_class;             // kernel classes of one iteration, launch order
     std::vector<cudaEvent_t> prof_ev;        // prof_class.size() + 1 per captured iteration
+    std::vector<char> prof_ran;              // per captured iteration and class slot: launched
     double prof_ms[LGK_K_COUNT] = {0};
     long long prof_n[LGK_K_COUNT] = {0};
     ~ResultData();
@@ -127,12 +133,16 @@ int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
           double* C, int ldc);
 
 // Tensor-core GEMMs (tc_gemm.cu)
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first);
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt);
 int sm_count();
 struct IterCtx;
 IterCtx make_ctx_public(ResultData& r);
 int tc_prepare(ResultData& r);  // attributes + TMA maps, before capture
 int tc_gemm1(ResultData& r, bool pdl = false);     // part[s] = Ahat . R1^T over split s of the columns
+// c1 = A_lo . R1_hi^T, c2 = A_lo^T . V_hi^T (lo_refresh full iterations);
+// first_only: skipped unless it is the solve's first iteration
+int tc_gemm1_lo(ResultData& r, bool pdl = false, bool first_only = false);
+int tc_gemm2_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_solve(ResultData& r, bool pdl = false);     // part[s] = G3 . rhs^T  (6 products)
 int tc_gemm2(ResultData& r, bool pdl = false);     // fused: q1, R1 update from Ahat^T . V
 

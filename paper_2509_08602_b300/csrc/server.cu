@@ -65,7 +65,7 @@ struct Request {
 // L^{-1} in FP64) and the solve's state and scratch.
 size_t request_footprint(int n_iso, int n_pts, int K, int precision) {
     const size_t B = 24ull * n_iso, m = B + n_iso, n = (size_t)n_pts + 8ull * n_iso;
-    const size_t mp = (size_t)round_up((long long)m, 128), np = (size_t)round_up((long long)n, 128);
+    const size_t mp = (size_t)round_up((long long)m, 256), np = (size_t)round_up((long long)n, 256);
     const size_t a_res = precision == LGK_PREC_FP32 ? 4 * mp * np : (precision == LGK_PREC_BF16 ? 2 : 4) * mp * np;
     const size_t g_res = precision == LGK_PREC_FP32 ? 4 * mp * mp : 6 * mp * mp;
     const size_t setup = std::max<size_t>({8 * mp * np + 8 * (size_t)n_pts * B, 8 * mp * np + 8 * mp * mp,

@@ -326,7 +326,8 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
     cudaStream_t st = cs.stream;
     const int P = d.n_pts, N = d.n_iso, B = 24 * N;
     const int m = B + N, n = P + 8 * N;
-    const int m_pad = (int)round_up(m, 128), n_pad = (int)round_up(n, 128);
+    // multiples of 256: the GEMMs may run 256-row tiles over either dimension
+    const int m_pad = (int)round_up(m, 256), n_pad = (int)round_up(n, 256);
     const int T = d.n_targets;
     cs.n_iso = N; cs.n_pts = P; cs.n_beams = B; cs.m = m; cs.n = n;
     cs.m_pad = m_pad; cs.n_pad = n_pad;

@@ -106,11 +106,6 @@ __device__ inline uint64_t policy_evict_first() {
     return p;
 }
 
-// Asynchronous L2 prefetch of `bytes` (multiple of 16) at a 16-byte aligned address.
-__device__ inline void prefetch_l2(const void* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -189,16 +184,17 @@ __host__ __device__ constexpr uint32_t instr_desc(int n, bool a_mn_major) {
 }
 
 // term t of an NT-term product: which A part and which B part.
+//   NT = 1: A.B (one part each: the lagged low-term products)
 //   NT = 2: A.B_hi + A.B_lo
 //   NT = 3: A_hi.B_hi + A_hi.B_lo + A_lo.B_hi
 //   NT = 6: all (a, b) with a + b <= 2 over three parts each
 // (dropped terms are below 2^-16 resp. 2^-24 of the product, relative).
 __host__ __device__ constexpr int term_a(int NT, int t) {
-    return NT == 2 ? 0 : NT == 3 ? (t == 2 ? 1 : 0)
+    return NT <= 2 ? 0 : NT == 3 ? (t == 2 ? 1 : 0)
                                : (t == 0 || t == 1 || t == 3 ? 0 : (t == 2 || t == 4 ? 1 : 2));
 }
 __host__ __device__ constexpr int term_b(int NT, int t) {
-    return NT == 2 ? t : NT == 3 ? (t == 1 ? 1 : 0)
+    return NT == 1 ? 0 : NT == 2 ? t : NT == 3 ? (t == 1 ? 1 : 0)
                                : (t == 0 || t == 2 || t == 5 ? 0 : (t == 1 || t == 4 ? 1 : 2));
 }
 
@@ -215,6 +211,8 @@ struct TcArgs {
     int nbuf;               // accumulators in TMEM (2 or 4; nbuf * tmem_cols <= 512)
     int stages;
     int stage_bytes;
+    int out_ld;             // EPI_STORE: rows of the output matrix (m_pad or n_pad)
+    int first_only;         // do the work only in the solve's first iteration (else return)
     float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
     void* out;              // EPI_RHS: rhs [3][Kp][m_pad]; EPI_SOLVE: V [2][Kp][m_pad];
                             // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
@@ -231,8 +229,10 @@ struct TcArgs {
 //   EPI_SOLVE  v = S^{-1} rhs: q2' = v + P2(q2), v split into two BF16 terms,
 //              residual partials of the m-block
 //   EPI_Q1     W = A^T V: q1' = P1(q1) - c/rho - W, R1' = 2 P1(q1') - q1' - c/rho
-//              as two BF16 terms, residual partials of the n-block
-enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3 };
+//              as two BF16 terms, residual partials of the n-block (W plus the
+//              lagged low-term product lo^T v when iterating with A_hi)
+//   EPI_STORE  the product as FP32 [Kp][out_ld] (the lagged low-term products)
+enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3, EPI_STORE = 4 };
 
 constexpr int kThreads = 320;               // 2 producer/MMA warps + 8 epilogue warps
 constexpr int kEpiThreads = 256;
@@ -250,7 +250,11 @@ __device__ inline void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory")
 template <int EPI>
 __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j0, const float v[kChunk],
                               float res[kChunk][5]) {
-    if (EPI == EPI_RHS) {
+    if (EPI == EPI_STORE) {
+        float* o = static_cast<float*>(a.out) + (size_t)j0 * a.out_ld + row;
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) o[(size_t)c * a.out_ld] = v[c];
+    } else if (EPI == EPI_RHS) {
         const size_t plane = (size_t)cx.Kp * cx.m_pad;
         const float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
         float q[kChunk], wb[kChunk];
@@ -307,22 +311,24 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
         const int sl = cx.col_slot[row];
         const float c_p = cx.c_slot[sl];
-        float q[kChunk], u[kChunk], ir[kChunk];
+        float q[kChunk], u[kChunk], ir[kChunk], w[kChunk];
         int act[kChunk];
         // the chunk's 8 columns share one word of the point selection (j0 % 8 == 0)
         const uint32_t sel =
             cx.mask ? __ldg(cx.mask + (size_t)row * cx.mask_words + (j0 >> 5)) >> (j0 & 31) : 0xffu;
+        const float* c2p = cx.c2 ? cx.c2 + (size_t)j0 * cx.n_pad + row : nullptr;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
             q[c] = q1p[(size_t)c * cx.n_pad];
             u[c] = ((sel >> c) & 1u) ? __ldg(cx.utab + (j0 + c) * cx.n_slot + sl) : 0.0f;
             ir[c] = __ldg(cx.inv_rho + j0 + c);
             act[c] = cx.active[j0 + c];
+            w[c] = c2p ? v[c] + __ldcg(c2p + (size_t)c * cx.n_pad) : v[c];
         }
         __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.n_pad + row;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) {
-            Q1Update qq = q1_update(q[c], v[c], u[c], c_p * ir[c]);
+            Q1Update qq = q1_update(q[c], w[c], u[c], c_p * ir[c]);
             const size_t o = (size_t)c * cx.n_pad;
             if (act[c]) q1p[o] = qq.qn;
             __nv_bfloat16 hi, lo;
@@ -360,7 +366,11 @@ __device__ inline void epi_resid(float res[kChunk][5], float* red, double* dst, 
     epi_bar();
 }
 
-template <int NA, int NB, int NT, bool A_MN, int EPI>
+// MT: 128-row sub-tiles per output tile.  MT = 2 puts two accumulators side by
+// side (256 rows) on one B tile: half the B traffic per A byte, and twice the
+// A bytes per pipeline stage, so more of A is in flight per SM (the one-term-A
+// GEMMs are otherwise limited by how much of A the stage ring holds).
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs a, IterCtx cx) {
@@ -387,14 +397,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[2 * S + 4 + b]), 8);   // one per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * a.tmem_cols);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * MT * a.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     // set-up done; from here on the previous kernel's output is read
     pdl_wait();
-    const bool run = ctrl->n_active != 0 && ctrl->err == 0;
+    const bool run = ctrl->n_active != 0 && ctrl->err == 0 && (!a.first_only || ctrl->iter == 0);
 
     if (!run) {
         // every column has stopped (or an error is pending): nothing to do
@@ -407,28 +417,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t pol_a = policy_evict_first();
         for (int sg = s0; sg < s1 && ok; ++sg) {
             const int* g = a.seg + 5 * sg;
-            const int row0 = g[0] * 128, col0 = g[1] * a.n_tile;
+            const int row0 = g[0] * 128 * MT, col0 = g[1] * a.n_tile;
             for (int kb = g[2]; kb < g[3] && ok; ++kb, ++it) {
                 const int s = it % S;
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
                 ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
                 if (!ok) break;
-                if (EPI == EPI_Q1 && kb == max(g[2], g[3] - 8)) {
-                    // the q1 rows this segment's epilogue reads: into L2 a few
-                    // stages before the accumulator completes (512 B per column)
-                    for (int j = 0; j < a.n_tile; ++j)
-                        prefetch_l2(cx.q1 + (size_t)(col0 + j) * cx.n_pad + row0, 512u);
-                }
                 const uint32_t full = smem_u32(&bars[s]);
                 const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
                 mbar_expect_tx(full, (uint32_t)a.stage_bytes);
                 const int kx = kb * 64;
                 if (A_MN) {
 #pragma unroll
-                    for (int p = 0; p < NA; ++p) {
-                        tma_load_3d_hint(st + p * kABytes, &tmA, row0, kx, p, full, pol_a);
-                        tma_load_3d_hint(st + p * kABytes + kABytes / 2, &tmA, row0 + 64, kx, p, full, pol_a);
-                    }
+                    for (int p = 0; p < NA; ++p)
+#pragma unroll
+                        for (int h = 0; h < MT; ++h) {
+                            const uint32_t dst = st + (p * MT + h) * kABytes;
+                            tma_load_3d_hint(dst, &tmA, row0 + h * 128, kx, p, full, pol_a);
+                            tma_load_3d_hint(dst + kABytes / 2, &tmA, row0 + h * 128 + 64, kx, p, full, pol_a);
+                        }
                 } else if (EPI == EPI_PARTIAL && NT == 6) {
                     // the solve: S^{-1} is re-read every iteration, default policy
                     // (an evict-last hint did not keep its 6 m^2 bytes in L2)
@@ -437,9 +444,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
 #pragma unroll
                     for (int p = 0; p < NA; ++p)
-                        tma_load_3d_hint(st + p * kABytes, &tmA, kx, row0, p, full, pol_a);
+#pragma unroll
+                        for (int h = 0; h < MT; ++h)
+                            tma_load_3d_hint(st + (p * MT + h) * kABytes, &tmA, kx, row0 + h * 128, p, full,
+                                             pol_a);
                 }
-                const uint32_t sb = st + NA * kABytes;
+                const uint32_t sb = st + NA * MT * kABytes;
 #pragma unroll
                 for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &tmB, kx, col0, p, full);
             }
@@ -457,25 +467,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int b = u % NBUF;
             if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 4 + b]), (uint32_t)((u / NBUF) & 1) ^ 1u, err);
             tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(b * a.tmem_cols);
+            const uint32_t d = tmem + (uint32_t)(b * MT * a.tmem_cols);
             for (int kb = g[2]; kb < g[3]; ++kb, ++it) {
                 const int s = it % S;
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
                 if (ok) ok = mbar_wait(smem_u32(&bars[s]), ph, err);
                 tc_fence_after();
                 const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-                const uint32_t sb = st + NA * kABytes;
+                const uint32_t sb = st + NA * MT * kABytes;
                 if (ok) {
 #pragma unroll
                     for (int t = 0; t < NT; ++t) {
-                        const uint32_t sa = st + term_a(NT, t) * kABytes;
                         const uint32_t sbt = sb + term_b(NT, t) * b_bytes;
 #pragma unroll
-                        for (int ks = 0; ks < 4; ++ks) {
-                            uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
-                                               : smem_desc(sa + ks * 32, 16, 1024);
-                            uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
-                            tc_mma(d, ad, bd, idesc, (kb > g[2] || t > 0 || ks > 0) ? 1u : 0u);
+                        for (int h = 0; h < MT; ++h) {
+                            const uint32_t sa = st + (term_a(NT, t) * MT + h) * kABytes;
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
+                                                   : smem_desc(sa + ks * 32, 16, 1024);
+                                uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
+                                tc_mma(d + (uint32_t)(h * a.tmem_cols), ad, bd, idesc,
+                                       (kb > g[2] || t > 0 || ks > 0) ? 1u : 0u);
+                            }
                         }
                     }
                 }
@@ -486,12 +500,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ---------------- epilogue (8 warps)
         const int ew = warp & 3;                        // TMEM lane quarter of this warp
-        const int hf = (warp - 2) >> 2;                 // column half
+        const int hf = (warp - 2) >> 2;                 // MT = 1: column half; MT = 2: row half
         const int et = threadIdx.x - 64;                // 0..255
-        const int r = ew * 32 + lane;                   // row within the tile
+        const int r = ew * 32 + lane;                   // row within the 128-row sub-tile
+        const int hrow = MT == 2 ? hf : 0;              // this warp's 128-row sub-tile
         const int half = a.n_tile / 2;                  // multiple of kChunk
-        const int cbeg = hf * half, cend = cbeg + half;
-        const bool check = EPI != EPI_PARTIAL && EPI != EPI_RHS && is_check_iter(ctrl, cx.check_every, cx.tol);
+        const int cbeg = MT == 2 ? 0 : hf * half, cend = MT == 2 ? a.n_tile : cbeg + half;
+        const bool check = (EPI == EPI_SOLVE || EPI == EPI_Q1) && is_check_iter(ctrl, cx.check_every, cx.tol);
         bool ok = true;
         for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
             const int b = u % NBUF;
@@ -499,14 +514,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int rt = g[0], ct = g[1], slot = g[4];
             const int tile = ct * a.row_tiles + rt;
             const int sb = a.tile_begin[tile], se = a.tile_begin[tile + 1];
-            const int row = rt * 128 + r, col0 = ct * a.n_tile;
-            double* rdst = cx.resid + ((size_t)((EPI == EPI_SOLVE ? cx.n_resid_n : 0) + rt) * cx.Kp + col0) * 5;
+            const int row = (rt * MT + hrow) * 128 + r, col0 = ct * a.n_tile;
+            double* rdst = cx.resid +
+                           ((size_t)((EPI == EPI_SOLVE ? cx.n_resid_n : 0) + rt * MT + hrow) * cx.Kp + col0) * 5;
             if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
             tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(b * a.tmem_cols);
+            const uint32_t base =
+                tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((b * MT + hrow) * a.tmem_cols);
             if (EPI == EPI_PARTIAL || se - sb > 1) {
-                // store this segment's partial sum in its slot
-                float* own = a.part + (size_t)slot * a.n_tile * 128 + r;
+                // store this segment's partial sum in its slot ([slot][MT][n_tile][128])
+                float* own = a.part + ((size_t)slot * MT + hrow) * a.n_tile * 128 + r;
                 for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
                     float v[kChunk];
                     tmem_ld8(base + (uint32_t)c0, v);
@@ -529,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
                             for (int k = sb; k < se; ++k) {
-                                const float* ps = a.part + (size_t)a.tile_slots[k] * a.n_tile * 128 + r;
+                                const float* ps = a.part + ((size_t)a.tile_slots[k] * MT + hrow) * a.n_tile * 128 + r;
 #pragma unroll
                                 for (int c = 0; c < kChunk; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
                             }
@@ -560,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, NBUF * a.tmem_cols);
+        tmem_dealloc(tmem, NBUF * MT * a.tmem_cols);
     }
 }
 
@@ -623,7 +640,7 @@ int sm_count() {
 // Stream-K plan: the units (column tile, row tile, k block), in that order,
 // cut into `grid` contiguous runs of equal length (+-1), each run split into
 // segments at tile boundaries.  Depends only on the GEMM's shape.
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first) {
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt) {
     const long long T = (long long)rows * col_tiles;
     const long long U = T * kb_total;
     const int grid = (int)std::min<long long>(sm_count(), U);
@@ -681,6 +698,7 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, b
     P.tile_count = d0;
     const int* d = d0 + rows * col_tiles;
     P.grid = grid;
+    P.mt = mt;
     P.nseg = nseg;
     P.rows = rows;
     P.col_tiles = col_tiles;
@@ -692,10 +710,15 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, b
     return LGK_OK;
 }
 
-template <int NA, int NB, int NT, bool A_MN, int EPI>
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
-                  void* out, bool pdl) {
+                  void* out, bool pdl, bool first_only = false) {
+    if (P.mt != MT) {
+        set_error("tensor-core GEMM: plan built for another tile height");
+        return LGK_EINVAL;
+    }
     TcArgs a{};
+    a.first_only = first_only;
     a.cta_seg = P.cta_seg;
     a.seg = P.seg;
     a.tile_begin = P.tile_begin;
@@ -705,7 +728,8 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     a.n_tile = P.n_tile;
     a.part = r.part.as<float>();
     a.out = out;
-    a.stage_bytes = NA * kABytes + NB * a.n_tile * 128;
+    a.out_ld = A_MN ? r.cs->n_pad : r.cs->m_pad;
+    a.stage_bytes = NA * MT * kABytes + NB * a.n_tile * 128;
     a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
     if (a.stages < 2) {
         set_error("tensor-core GEMM: stage does not fit in shared memory");
@@ -713,10 +737,14 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     }
     a.tmem_cols = 32;
     while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
-    a.nbuf = 4 * a.tmem_cols <= 512 ? 4 : 2;
+    a.nbuf = 4 * MT * a.tmem_cols <= 512 ? 4 : 2;
+    if (a.nbuf * MT * a.tmem_cols > 512) {
+        set_error("tensor-core GEMM: accumulators exceed tensor memory");
+        return LGK_EINVAL;
+    }
     size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
-    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI>, dim3(P.grid), dim3(kThreads), smem, r.cs->stream,
-                          pdl, mA, mB, a, make_ctx_public(r)));
+    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem,
+                          r.cs->stream, pdl, mA, mB, a, make_ctx_public(r)));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -726,6 +754,14 @@ static int maps_for(ResultData& r, TcMaps& M) {
     int rc;
     if ((rc = make_map(&M.A_k, cs.Ahat.p, cs.n_pad, cs.m_pad, cs.na, 128))) return rc;
     if ((rc = make_map(&M.A_mn, cs.Ahat.p, cs.n_pad, cs.m_pad, cs.na, 64))) return rc;
+    if (cs.na == 2) {       // the low BF16 term alone
+        const void* lo = static_cast<const char*>(cs.Ahat.p) + (size_t)cs.m_pad * cs.n_pad * 2;
+        if ((rc = make_map(&M.Alo_k, lo, cs.n_pad, cs.m_pad, 1, 128))) return rc;
+        if ((rc = make_map(&M.Alo_mn, lo, cs.n_pad, cs.m_pad, 1, 64))) return rc;
+    } else {
+        M.Alo_k = M.A_k;
+        M.Alo_mn = M.A_mn;
+    }
     if ((rc = make_map(&M.G3, cs.G3.p, cs.m_pad, cs.m_pad, 3, 128))) return rc;
     if ((rc = make_map(&M.R1, r.R1.p, cs.n_pad, r.Kp, 2, r.n_tile))) return rc;
     if ((rc = make_map(&M.rhs, r.rhs.p, cs.m_pad, r.Kp, 3, r.n_tile_s))) return rc;
@@ -733,9 +769,9 @@ static int maps_for(ResultData& r, TcMaps& M) {
     return LGK_OK;
 }
 
-template <int NA, int NB, int NT, bool A_MN, int EPI>
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int set_smem_attr() {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) {
         set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -753,19 +789,47 @@ int tc_prepare(ResultData& r) {
     if ((rc = set_smem_attr<3, 3, 6, false, EPI_PARTIAL>())) return rc;
     if ((rc = set_smem_attr<1, 2, 2, true, EPI_Q1>())) return rc;
     if ((rc = set_smem_attr<2, 2, 3, true, EPI_Q1>())) return rc;
+    if ((rc = set_smem_attr<1, 1, 1, false, EPI_STORE>())) return rc;
+    if ((rc = set_smem_attr<1, 1, 1, true, EPI_STORE>())) return rc;
+    if ((rc = set_smem_attr<1, 2, 2, false, EPI_PARTIAL, 2>())) return rc;
+    if ((rc = set_smem_attr<1, 2, 2, true, EPI_Q1, 2>())) return rc;
+    if ((rc = set_smem_attr<1, 1, 1, false, EPI_STORE, 2>())) return rc;
+    if ((rc = set_smem_attr<1, 1, 1, true, EPI_STORE, 2>())) return rc;
     if ((rc = maps_for(r, r.maps))) return rc;
+    // 256-row tiles for the GEMMs whose A operand is one BF16 term (the
+    // one-term form, or A_hi and A_lo with lo_refresh) when two accumulators
+    // fit in tensor memory next to each other
+    r.wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
+    const int hm = r.wide ? 2 : 1;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
-    if ((rc = build_plan(r.plan1, mt, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false))) return rc;
-    if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s, false))) return rc;
-    if ((rc = build_plan(r.plan2, nt, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true))) return rc;
-    size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile, (size_t)r.plan_s.nseg * r.n_tile_s,
-                             (size_t)r.plan2.nseg * r.n_tile});
+    if ((rc = build_plan(r.plan1, mt / hm, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false, hm))) return rc;
+    if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s, false, 1))) return rc;
+    if ((rc = build_plan(r.plan2, nt / hm, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true, hm))) return rc;
+    size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile * hm, (size_t)r.plan_s.nseg * r.n_tile_s,
+                             (size_t)r.plan2.nseg * r.n_tile * hm});
     return r.part.alloc(slots * 128 * 4);
 }
 
+// With lo_refresh the heavy products use A_hi (NA = 1: plane 0 of the
+// two-term maps) and the low term comes from tc_gemm1_lo / tc_gemm2_lo.
+int tc_gemm1_lo(ResultData& r, bool pdl, bool first_only) {
+    if (r.wide)
+        return launch<1, 1, 1, false, EPI_STORE, 2>(r.maps.Alo_k, r.maps.R1, r.plan1, r, r.c1.p, pdl,
+                                                    first_only);
+    return launch<1, 1, 1, false, EPI_STORE>(r.maps.Alo_k, r.maps.R1, r.plan1, r, r.c1.p, pdl, first_only);
+}
+
+int tc_gemm2_lo(ResultData& r, bool pdl, bool first_only) {
+    if (r.wide)
+        return launch<1, 1, 1, true, EPI_STORE, 2>(r.maps.Alo_mn, r.maps.V, r.plan2, r, r.c2.p, pdl,
+                                                   first_only);
+    return launch<1, 1, 1, true, EPI_STORE>(r.maps.Alo_mn, r.maps.V, r.plan2, r, r.c2.p, pdl, first_only);
+}
+
 int tc_gemm1(ResultData& r, bool pdl) {
-    if (r.cs->na == 2)
+    if (r.cs->na == 2 && !r.refine)
         return launch<2, 2, 3, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr, pdl);
+    if (r.wide) return launch<1, 2, 2, false, EPI_PARTIAL, 2>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr, pdl);
     return launch<1, 2, 2, false, EPI_PARTIAL>(r.maps.A_k, r.maps.R1, r.plan1, r, nullptr, pdl);
 }
 
@@ -774,7 +838,8 @@ int tc_solve(ResultData& r, bool pdl) {
 }
 
 int tc_gemm2(ResultData& r, bool pdl) {
-    if (r.cs->na == 2) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    if (r.cs->na == 2 && !r.refine) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    if (r.wide) return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
     return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
 }
 

@@ -43,7 +43,7 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("normalize_rows", C.c_int), ("scale_bot", C.c_int),
                 ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("lo_refresh", C.c_int)]
 
 
 class ServerParams(C.Structure):
@@ -396,7 +396,8 @@ def fetch_state(res: Result):
     return q1, q2
 
 
-KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "q1_update", "finalize")
+KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "q1_update", "finalize",
+           "gemm1_lo", "gemm2_lo")
 
 
 def fetch_profile(res: Result) -> dict:

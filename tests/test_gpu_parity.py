@@ -111,7 +111,7 @@ def test_short_trajectory_from_zero(lgk, cfg0, prec):
     """Five iterations from z = y = 0 (cold start); rounding differences grow
     along the trajectory, so the bound is five one-step bounds."""
     c = cfg0
-    cs = make(lgk, c["case"], prec)
+    cs = make(lgk, c["case"], prec, lo_refresh=0)
     A = lp_matrix(c["lp"], lgk, prec)
     tol = 5 * np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, prec, A.shape[1])
     res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=5)
@@ -126,11 +126,34 @@ def test_short_trajectory_from_zero(lgk, cfg0, prec):
     assert np.all(g2.T - np.minimum(g2.T, c["b"]) >= 0)
 
 
+def test_lagged_low_term_trajectory(lgk, cfg0):
+    """The default two-term iteration (lo_refresh = 1): light steps with A_hi
+    plus the low term's products from the last full step.  25 iterations from
+    zero (full at 1, 10, 20) against the oracle's lagged variant on the same
+    two-term matrix; the bound is 25 one-step bounds."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    lp = c["lp"]
+    hi = L.bf16_round(lp.A)
+    A = hi + L.bf16_round(lp.A - hi)
+    tol = 25 * np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, 2, A.shape[1])
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=25)
+    g1, g2 = lgk.fetch_state(res)
+    o = AD.admm(A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=25, lagged_lo=(hi, 10, 0))
+    r1, r2 = o.z1 + o.y1, o.z2 + o.y2
+    assert np.abs(g1.T - r1).max() <= tol * np.abs(r1).max()
+    assert np.abs(g2.T - r2).max() <= tol * np.abs(r2).max()
+    # the light steps ran: 3 full steps (1, 10, 20) of 25
+    prof_cs = make(lgk, c["case"], 2, profile=1)
+    p = lgk.fetch_profile(lgk.solve_weightings(prof_cs, c["W"], c["rho"], tol=0.0, max_iter=25))
+    assert p["gemm1_lo"][1] == 3 and p["gemm2_lo"][1] == 3 and p["gemm1"][1] == 25
+
+
 def test_warm_start_resumes_the_iteration(lgk, cfg0):
     """Checkpoint / resume: 30 iterations, fetch the state, 20 more from it
     equals 50 straight (same arithmetic, bit for bit)."""
     c = cfg0
-    cs = make(lgk, c["case"], 2)
+    cs = make(lgk, c["case"], 2, lo_refresh=0)
     a = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=30)
     q1, q2 = lgk.fetch_state(a)
     b = lgk.solve_weightings_warm(cs, c["W"], c["rho"], q1_init=q1, q2_init=q2, tol=0.0, max_iter=20)

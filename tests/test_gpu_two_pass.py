@@ -9,7 +9,7 @@ second-pass solve, each against the oracle.
   * masked iteration: one ADMM iteration from a common state, element by
     element, within ||A||_2^2 u max|q| (the unmasked bound; a masked point
     only clips at 0);
-  * second-pass plans: converged (tol 1e-4) with the relative objective gap
+  * second-pass plans: converged (tol 5e-5) with the relative objective gap
     <= 1e-3 against the simplex optimum of each weighting's own LP, assembled
     independently from its selected points only.
 """
@@ -24,7 +24,9 @@ from synth import cases as SC
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-4
+TOL = 5e-5                 # residuals within the 1e-4 gate with headroom for the 1e-3 objective
+                           # gap (a stop at 1e-4 alone does not bound the gap: the FP64 oracle
+                           # itself stops at gaps up to 7.3e-4 there)
 DELTA = (1.0, 0.5)         # Delta of the LD1 (10 Gy) and LD2 (5 Gy) volumes
 N_LD = (60, 60)            # desired low-dose points per weighting and level
 SEED = 20250910
