@@ -242,6 +242,52 @@ constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile
 
 __device__ inline void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// The q1 step (EPI_Q1) in two halves, so the epilogue can load one chunk's
+// inputs while it finishes the previous one.
+struct Q1In {
+    float q[kChunk], u[kChunk], ir[kChunk], c2[kChunk];
+    int act[kChunk];
+    float c_p;
+};
+
+__device__ inline void q1_load(const IterCtx& cx, int row, int j0, Q1In& in) {
+    const float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
+    const int sl = cx.col_slot[row];
+    in.c_p = cx.c_slot[sl];
+    // the chunk's 8 columns share one word of the point selection (j0 % 8 == 0)
+    const uint32_t sel =
+        cx.mask ? __ldg(cx.mask + (size_t)row * cx.mask_words + (j0 >> 5)) >> (j0 & 31) : 0xffu;
+    const float* c2p = cx.c2 ? cx.c2 + (size_t)j0 * cx.n_pad + row : nullptr;
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c) {
+        in.q[c] = q1p[(size_t)c * cx.n_pad];
+        in.u[c] = ((sel >> c) & 1u) ? __ldg(cx.utab + (j0 + c) * cx.n_slot + sl) : 0.0f;
+        in.ir[c] = __ldg(cx.inv_rho + j0 + c);
+        in.act[c] = cx.active[j0 + c];
+        in.c2[c] = c2p ? __ldcg(c2p + (size_t)c * cx.n_pad) : 0.0f;
+    }
+}
+
+// W = v (+ the lagged lo^T v): q1' = P1(q1) - c/rho - W, R1' as two BF16 terms.
+__device__ inline void q1_finish(const IterCtx& cx, const TcArgs& a, int row, int j0, const float v[kChunk],
+                                 const Q1In& in, float res[kChunk][5]) {
+    const size_t plane = (size_t)cx.Kp * cx.n_pad;
+    float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
+    __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.n_pad + row;
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c) {
+        Q1Update qq = q1_update(in.q[c], v[c] + in.c2[c], in.u[c], in.c_p * in.ir[c]);
+        const size_t o = (size_t)c * cx.n_pad;
+        if (in.act[c]) q1p[o] = qq.qn;
+        __nv_bfloat16 hi, lo;
+        split_bf16(qq.r1, hi, lo);
+        d[o] = hi;
+        d[plane + o] = lo;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) res[c][k] = qq.res[k];
+    }
+}
+
 // Apply the element-wise step to kChunk columns [j0, j0 + kChunk) of row `row`,
 // accumulating the 5 residual terms per column (block-reduced by the caller).
 // Only 8 warps per SM run this, so every input of the chunk's columns is loaded
@@ -307,37 +353,9 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
             res[c][0] = r * r; res[c][1] = x * x; res[c][2] = zn * zn; res[c][3] = s * s; res[c][4] = yn * yn;
         }
     } else {
-        const size_t plane = (size_t)cx.Kp * cx.n_pad;
-        float* q1p = cx.q1 + (size_t)j0 * cx.n_pad + row;
-        const int sl = cx.col_slot[row];
-        const float c_p = cx.c_slot[sl];
-        float q[kChunk], u[kChunk], ir[kChunk], w[kChunk];
-        int act[kChunk];
-        // the chunk's 8 columns share one word of the point selection (j0 % 8 == 0)
-        const uint32_t sel =
-            cx.mask ? __ldg(cx.mask + (size_t)row * cx.mask_words + (j0 >> 5)) >> (j0 & 31) : 0xffu;
-        const float* c2p = cx.c2 ? cx.c2 + (size_t)j0 * cx.n_pad + row : nullptr;
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            q[c] = q1p[(size_t)c * cx.n_pad];
-            u[c] = ((sel >> c) & 1u) ? __ldg(cx.utab + (j0 + c) * cx.n_slot + sl) : 0.0f;
-            ir[c] = __ldg(cx.inv_rho + j0 + c);
-            act[c] = cx.active[j0 + c];
-            w[c] = c2p ? v[c] + __ldcg(c2p + (size_t)c * cx.n_pad) : v[c];
-        }
-        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.n_pad + row;
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            Q1Update qq = q1_update(q[c], w[c], u[c], c_p * ir[c]);
-            const size_t o = (size_t)c * cx.n_pad;
-            if (act[c]) q1p[o] = qq.qn;
-            __nv_bfloat16 hi, lo;
-            split_bf16(qq.r1, hi, lo);
-            d[o] = hi;
-            d[plane + o] = lo;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) res[c][k] = qq.res[k];
-        }
+        Q1In in;
+        q1_load(cx, row, j0, in);
+        q1_finish(cx, a, row, j0, v, in, res);
     }
 }
 
@@ -557,6 +575,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     epi_bar();
                 }
+            } else if (EPI == EPI_Q1) {
+                // the whole k range of the tile is in this accumulator; the
+                // next chunk's inputs load while this one is finished
+                // (two named buffers, unrolled by two, so both stay in registers)
+                Q1In inA, inB;
+                float vA[kChunk], vB[kChunk], res[kChunk][5];
+                q1_load(cx, row, col0 + cbeg, inA);
+                tmem_ld8(base + (uint32_t)cbeg, vA);
+                for (int c0 = cbeg; c0 < cend; c0 += 2 * kChunk) {
+                    const bool moreB = c0 + kChunk < cend;
+                    if (moreB) q1_load(cx, row, col0 + c0 + kChunk, inB);
+                    if (!ok)
+                        for (int c = 0; c < kChunk; ++c) vA[c] = 0.f;
+                    q1_finish(cx, a, row, col0 + c0, vA, inA, res);
+                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
+                    if (!moreB) break;
+                    tmem_ld8(base + (uint32_t)(c0 + kChunk), vB);
+                    const bool moreA = c0 + 2 * kChunk < cend;
+                    if (moreA) q1_load(cx, row, col0 + c0 + 2 * kChunk, inA);
+                    if (!ok)
+                        for (int c = 0; c < kChunk; ++c) vB[c] = 0.f;
+                    q1_finish(cx, a, row, col0 + c0 + kChunk, vB, inB, res);
+                    if (check) epi_resid(res, red, rdst + (c0 + kChunk) * 5, lane, ew, hf, et);
+                    if (moreA) tmem_ld8(base + (uint32_t)(c0 + 2 * kChunk), vA);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
             } else {
                 // the whole k range of the tile is in this accumulator
                 for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
