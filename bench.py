@@ -299,7 +299,8 @@ def run_ours(args, rank, world, local):
     # the timed solves run without per-kernel events (those split the
     # iteration graph and stop consecutive kernels from overlapping); the
     # per-kernel durations come from a profiled solve of the same batch
-    params = lgk.default_params(precision=prec, device=local, profile=0, lo_refresh=int(refine))
+    params = lgk.default_params(precision=prec, device=local, profile=0, lo_refresh=int(refine),
+                                check_every=args.check_every)
     from synth import cases as SC
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
@@ -350,7 +351,7 @@ def run_ours(args, rank, world, local):
     cs_p = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                            case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                            params=lgk.default_params(precision=prec, device=local, profile=1,
-                                                     lo_refresh=int(refine)))
+                                                     lo_refresh=int(refine), check_every=args.check_every))
     r = lgk.solve_weightings(cs_p, W, None, **rule)
     for k, (ms, nl) in lgk.fetch_profile(r).items():
         prof[k][0] += ms
@@ -370,7 +371,8 @@ def run_ours(args, rank, world, local):
         c2 = lgk.create_case(phi_pinned, case.kind, case.struct_id, case.n_iso, case.d_presc,
                              case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                              params=lgk.default_params(precision=prec, device=local,
-                                                       lo_refresh=int(refine)))
+                                                       lo_refresh=int(refine),
+                                                       check_every=args.check_every))
         r = lgk.solve_weightings(c2, W, None, **rule)
         t, tau = lgk.fetch_times(r)
         conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
@@ -650,6 +652,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--check-every", type=int, default=10,
+                    help="iterations between residual tests (and low-term refreshes)")
     ap.add_argument("--exact", action="store_true",
                     help="both BF16 terms of A in every iteration (lo_refresh = 0)")
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS),
