@@ -82,6 +82,35 @@ __device__ inline float gemm_out(const SumSrc& s, int i, int j) {
     return acc;
 }
 
+// The same for rows i .. i+3 (i % 4 == 0, one 16-byte load per slot): the
+// slots of a tile hold 128 consecutive rows per column, so four rows of one
+// column are one aligned float4.
+__device__ inline float4 gemm_out4(const SumSrc& s, int i, int j) {
+    if (!s.tile_begin) return __ldcg(reinterpret_cast<const float4*>(s.part + (size_t)j * s.rows_pad + i));
+    const int ct = j / s.n_tile, t = ct * s.row_tiles + (i >> 7) / s.mt, h = (i >> 7) % s.mt;
+    const int b = __ldg(s.tile_begin + t), e = __ldg(s.tile_begin + t + 1);
+    const float4* p = reinterpret_cast<const float4*>(
+        s.part + (((size_t)b * s.mt + h) * s.n_tile + (j - ct * s.n_tile)) * 128 + (i & 127));
+    const size_t stride = (size_t)s.mt * s.n_tile * 32;      // in float4
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int k = 0;
+    for (; k + 4 <= e - b; k += 4) {
+        const float4 a0 = __ldcg(p + k * stride), a1 = __ldcg(p + (k + 1) * stride);
+        const float4 a2 = __ldcg(p + (k + 2) * stride), a3 = __ldcg(p + (k + 3) * stride);
+        acc.x += a0.x; acc.y += a0.y; acc.z += a0.z; acc.w += a0.w;
+        acc.x += a1.x; acc.y += a1.y; acc.z += a1.z; acc.w += a1.w;
+        acc.x += a2.x; acc.y += a2.y; acc.z += a2.z; acc.w += a2.w;
+        acc.x += a3.x; acc.y += a3.y; acc.z += a3.z; acc.w += a3.w;
+    }
+    for (; k < e - b; ++k) {
+        const float4 a = __ldcg(p + k * stride);
+        acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+    }
+    return acc;
+}
+
+__device__ inline float f4(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
 // Element-wise kernels over the m-block (one element per thread, grid
 // (m_pad / 256, Kp)) or the n-block; kCols is the column group of the
 // residual partials written per 128-row tile.
@@ -130,64 +159,86 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
 }
 
 // rhs = A R1 + q2 - 2 P2(q2).  Grid (m_pad / 128, Kp), 128 threads.
+// rhs = A R1 (+ the lagged lo R1) + q2 - 2 P2(q2), split into three BF16
+// parts (the solve amplifies input rounding).  Four rows per thread; grid
+// (m_pad / 256, Kp), 64 threads.
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
+__global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
     pdl_trigger();
     pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    const int i = blockIdx.x * 128 + threadIdx.x, j = blockIdx.y;
+    const int i = blockIdx.x * 256 + threadIdx.x * 4, j = blockIdx.y;
     const size_t o = (size_t)j * cx.m_pad + i;
-    const float acc = gemm_out(src, i, j) + (cx.c1 ? cx.c1[o] : 0.f);
-    const float q = cx.q2[o];
-    const float p2 = fminf(q, b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
-    const float r = acc + q - 2.f * p2;
-    if (BF16) {      // three BF16 parts: the solve amplifies input rounding
+    const float4 acc = gemm_out4(src, i, j);
+    const float4 c1 = cx.c1 ? __ldcg(reinterpret_cast<const float4*>(cx.c1 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 q = *reinterpret_cast<const float4*>(cx.q2 + o);
+    float r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float p2 = fminf(f4(q, k), b_of(i + k, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
+        r[k] = f4(acc, k) + f4(c1, k) + f4(q, k) - 2.f * p2;
+    }
+    if (BF16) {
         const size_t plane = (size_t)cx.Kp * cx.m_pad;
-        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(rhs);
-        __nv_bfloat16 hi = __float2bfloat16_rn(r);
-        float r1 = r - __bfloat162float(hi);
-        __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        d[o] = hi;
-        d[plane + o] = mid;
-        d[2 * plane + o] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+        __nv_bfloat16 hi[4], mid[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            hi[k] = __float2bfloat16_rn(r[k]);
+            const float r1 = r[k] - __bfloat162float(hi[k]);
+            mid[k] = __float2bfloat16_rn(r1);
+            lo[k] = __float2bfloat16_rn(r1 - __bfloat162float(mid[k]));
+        }
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(rhs) + o;
+        *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(hi);
+        *reinterpret_cast<uint2*>(d + plane) = *reinterpret_cast<const uint2*>(mid);
+        *reinterpret_cast<uint2*>(d + 2 * plane) = *reinterpret_cast<const uint2*>(lo);
     } else {
-        static_cast<float*>(rhs)[o] = r;
+        *reinterpret_cast<float4*>(static_cast<float*>(rhs) + o) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
 // v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block (one
-// per 128-row tile and column).  Grid (m_pad / 128, Kp), 128 threads.
+// per 128-row tile and column: one warp per 128 rows, four rows per thread).
+// Grid (m_pad / 256, Kp), 64 threads.
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
+__global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
     pdl_trigger();
     pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    const int rt = blockIdx.x, i = rt * 128 + threadIdx.x, j = blockIdx.y;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.y;
+    const int rt = blockIdx.x * 2 + w, i = rt * 128 + lane * 4;
     const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
     const size_t o = (size_t)j * cx.m_pad + i;
-    const float v = gemm_out(src, i, j);
-    const float qo = cx.q2[o];
-    const float bb = b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
-    const float zo = fminf(qo, bb);
-    const float qn = v + zo;
-    if (cx.active[j]) cx.q2[o] = qn;
+    const float4 v = gemm_out4(src, i, j);
+    const float4 qo = *reinterpret_cast<const float4*>(cx.q2 + o);
+    float qn[4], res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float bb = b_of(i + k, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
+        const float zo = fminf(f4(qo, k), bb);
+        qn[k] = f4(v, k) + zo;
+        const float yo = f4(qo, k) - zo, zn = fminf(qn[k], bb), yn = qn[k] - zn;
+        const float r = yn - yo, x = qn[k] - yo, sres = zn - zo;
+        res[0] += r * r; res[1] += x * x; res[2] += zn * zn; res[3] += sres * sres; res[4] += yn * yn;
+    }
+    if (cx.active[j]) *reinterpret_cast<float4*>(cx.q2 + o) = make_float4(qn[0], qn[1], qn[2], qn[3]);
     if (BF16) {
-        __nv_bfloat16 hi, lo;
-        split_bf16(v, hi, lo);
-        static_cast<__nv_bfloat16*>(V)[o] = hi;
-        static_cast<__nv_bfloat16*>(V)[(size_t)cx.Kp * cx.m_pad + o] = lo;
+        __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) split_bf16(f4(v, k), hi[k], lo[k]);
+        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(V) + o;
+        *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(hi);
+        *reinterpret_cast<uint2*>(d + (size_t)cx.Kp * cx.m_pad) = *reinterpret_cast<const uint2*>(lo);
     } else {
-        static_cast<float*>(V)[o] = v;
+        *reinterpret_cast<float4*>(static_cast<float*>(V) + o) = v;
     }
     if (check) {
-        const float yo = qo - zo, zn = fminf(qn, bb), yn = qn - zn;
-        const float r = yn - yo, x = qn - yo, s = zn - zo;
-        float res[5] = {r * r, x * x, zn * zn, s * s, yn * yn};
-        __shared__ double out[5];
-        block_sum5(res, out);
-        if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            for (int sh = 16; sh > 0; sh >>= 1) res[k] += __shfl_xor_sync(0xffffffffu, res[k], sh);
+        if (lane == 0) {
             double* dst = cx.resid + ((size_t)(cx.n_resid_n + rt) * cx.Kp + j) * 5;
-            for (int k = 0; k < 5; ++k) dst[k] = out[k];
+            for (int k = 0; k < 5; ++k) dst[k] = (double)res[k];
         }
     }
 }
@@ -391,8 +442,8 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 1);
-    dim3 gm(cs.m_pad / 128, r.Kp);
-    k_reduce_rhs<false><<<gm, 128, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
+    dim3 gm(cs.m_pad / 256, r.Kp);
+    k_reduce_rhs<false><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     // solve: part = rhs . G^T (G symmetric)
@@ -404,7 +455,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 3);
-    k_reduce_solve<false><<<gm, 128, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
+    k_reduce_solve<false><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     // GEMM2: W[Kp][n_pad] = V[Kp][m_pad] . A[m_pad][n_pad]
@@ -432,7 +483,7 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
     int rc;
-    dim3 gm(cs.m_pad / 128, r.Kp);
+    dim3 gm(cs.m_pad / 256, r.Kp);
     // consecutive kernels overlap launch and set-up with the predecessor's
     // tail (programmatic dependent launch), except across profiling events
     const bool pdl = r.prof_ev.empty();
@@ -453,12 +504,12 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     prof_mark(r, itx, 1);
     if ((rc = tc_gemm1(r, pdl && (itx > 0 || full)))) return rc;
     prof_mark(r, itx, 2);
-    LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p));
+    LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p));
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 3);
     if ((rc = tc_solve(r, pdl))) return rc;
     prof_mark(r, itx, 4);
-    LGK_CUDA_TRY(launch_k(k_reduce_solve<true>, gm, dim3(128), 0, st, pdl, cx, plan_src(r, r.plan_s), r.V.p));
+    LGK_CUDA_TRY(launch_k(k_reduce_solve<true>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan_s), r.V.p));
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 5);
     if (full && (rc = tc_gemm2_lo(r, pdl, first_only))) return rc;
