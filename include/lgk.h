@@ -99,12 +99,16 @@ typedef struct {
                                 (read by lgk_fetch_profile); default 0                       */
     int lo_refresh;          /* LGK_PREC_BF16X3 only.  1 (default): iterate with the high BF16
                                 term of A and add the low term's product from the last full
-                                iteration (lo R1 and lo^T v, kept in FP32); the first
-                                iteration of every graph replay and every residual-test
-                                iteration use both terms and refresh those products.  The
-                                fixed point, hence every converged plan, is that of the
-                                two-term A; the heavy products read half the bytes.
+                                iteration (lo R1 and lo^T v, kept in FP32); the solve's first
+                                iteration and every residual-test iteration use both terms
+                                and refresh those products.  The fixed point, hence every
+                                converged plan, is that of the two-term A; the heavy products
+                                read half the bytes.
                                 0: both terms every iteration (the literal iteration).      */
+    int lo_refresh_iters;    /* with lo_refresh = 1: once a solve has run this many iterations
+                                with columns still active, it continues with the literal
+                                iteration (a safety net for columns the lagged products slow
+                                down); 0 = never.  Default 8000.                             */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */

@@ -65,6 +65,7 @@ int lgk_default_params(lgk_params* p) {
     p->timeout_ms = 600000;
     p->profile = 0;
     p->lo_refresh = 1;
+    p->lo_refresh_iters = 8000;
     return LGK_OK;
 }
 
@@ -76,6 +77,7 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     lgk_default_params(&prm);
     if (p) prm = *p;
     if (prm.lo_refresh != 0 && prm.lo_refresh != 1) return fail(LGK_EINVAL, "lo_refresh must be 0 or 1");
+    if (prm.lo_refresh_iters < 0) return fail(LGK_EINVAL, "lo_refresh_iters must be >= 0");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

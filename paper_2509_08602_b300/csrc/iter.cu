@@ -664,34 +664,42 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
         r.prof_ran.assign((size_t)per_graph * kpi, 1);
     }
-    LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < per_graph; ++it) {
-        rc = bf16 ? iteration_bf16(r, cx, it) : iteration_fp32(r, cx, it);
-        if (rc) {
-            cudaStreamEndCapture(st, &g);
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-    }
-    LGK_CUDA_TRY(cudaStreamEndCapture(st, &g));
-    // kernels per replay: the graph's kernel nodes (the captured launches
-    // were counted at capture time, when nothing ran)
-    size_t n_nodes = 0, n_all = 0;
-    if (cudaGraphGetNodes(g, nullptr, &n_all) == cudaSuccess && n_all) {
-        std::vector<cudaGraphNode_t> nodes(n_all);
-        if (cudaGraphGetNodes(g, nodes.data(), &n_all) == cudaSuccess)
-            for (auto nd : nodes) {
-                cudaGraphNodeType ty;
-                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
+    size_t n_nodes = 0;
+    // capture the graph of `per_graph` iterations with the current ctx
+    auto capture = [&]() -> int {
+        LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < per_graph; ++it) {
+            int rc2 = bf16 ? iteration_bf16(r, cx, it) : iteration_fp32(r, cx, it);
+            if (rc2) {
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                return rc2;
             }
-    }
-    count_launch(-(long long)n_nodes);
-    cudaError_t e = cudaGraphInstantiate(&r.graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-        return LGK_ECUDA;
-    }
+        }
+        LGK_CUDA_TRY(cudaStreamEndCapture(st, &g));
+        // kernels per replay: the graph's kernel nodes (the captured launches
+        // were counted at capture time, when nothing ran)
+        size_t n_all = 0;
+        n_nodes = 0;
+        if (cudaGraphGetNodes(g, nullptr, &n_all) == cudaSuccess && n_all) {
+            std::vector<cudaGraphNode_t> nodes(n_all);
+            if (cudaGraphGetNodes(g, nodes.data(), &n_all) == cudaSuccess)
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
+                }
+        }
+        count_launch(-(long long)n_nodes);
+        cudaError_t e = cudaGraphInstantiate(&r.graph, g, 0);
+        cudaGraphDestroy(g);
+        g = nullptr;
+        if (e != cudaSuccess) {
+            set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            return LGK_ECUDA;
+        }
+        return LGK_OK;
+    };
+    if ((rc = capture())) return rc;
     r.graph_iters = per_graph;
 
     Control* hc = nullptr;
@@ -739,6 +747,16 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         }
         iter_before = hc->iter;
         if (hc->n_active == 0) break;
+        if (r.refine && cs.prm.lo_refresh_iters > 0 && hc->iter >= cs.prm.lo_refresh_iters) {
+            // columns still running this long: continue with the literal
+            // iteration (all terms every step) from the current state
+            cudaGraphExecDestroy(r.graph);
+            r.graph = nullptr;
+            r.refine = false;
+            if ((rc = tc_prepare(r))) break;
+            cx = make_ctx(r);
+            if ((rc = capture())) break;
+        }
     }
     cudaFreeHost(hc);
     if (rc) return rc;

@@ -43,7 +43,7 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("normalize_rows", C.c_int), ("scale_bot", C.c_int),
                 ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
-                ("profile", C.c_int), ("lo_refresh", C.c_int)]
+                ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int)]
 
 
 class ServerParams(C.Structure):

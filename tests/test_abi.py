@@ -68,6 +68,7 @@ def test_default_params(lgk):
     p = lgk.default_params()
     assert p.precision == lgk.PREC_BF16X3 and p.check_every == 10 and p.normalize_rows == 1
     assert p.scale_bot == 1 and p.eps_abs == 1e-12 and p.hbm_budget == 0 and p.lo_refresh == 1
+    assert p.lo_refresh_iters == 8000
 
 
 def test_null_arguments_are_errors_not_crashes(lgk):

@@ -354,3 +354,20 @@ def test_oar_and_unequal_prescriptions(lgk):
     for key in ("coverage", "selectivity", "bot"):
         rel = np.abs(met[key] - met_ref[key]) / np.abs(met_ref[key])
         assert rel.max() <= 5e-3, (key, rel)
+
+
+def test_lagged_iteration_gives_way_to_the_literal_one(lgk, cfg0):
+    """lo_refresh_iters: a solve still running after that many iterations
+    continues with the literal iteration (new tile plans, a recaptured
+    graph, the same state) and converges to the same plans."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2, lo_refresh_iters=30, profile=1)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    gap = np.abs(st["obj"] - c["opt"]) / np.maximum(1.0, np.abs(c["opt"]))
+    assert gap.max() <= 1e-3
+    p = lgk.fetch_profile(res)
+    # lagged products only in the first graph replay (50 iterations): 1 + 5 full steps
+    assert p["gemm1_lo"][1] == 6 and p["gemm2_lo"][1] == 6
+    assert p["gemm1"][1] == int(st["iters"].max())
