@@ -371,3 +371,25 @@ def test_lagged_iteration_gives_way_to_the_literal_one(lgk, cfg0):
     # lagged products only in the first graph replay (50 iterations): 1 + 5 full steps
     assert p["gemm1_lo"][1] == 6 and p["gemm2_lo"][1] == 6
     assert p["gemm1"][1] == int(st["iters"].max())
+
+
+def test_wide_batch_two_column_tiles(lgk, cfg0):
+    """K = 300 weightings: two column tiles of up to 160 columns, so the
+    lagged form runs its 128-row-tile kernels (two accumulators of that
+    width do not fit tensor memory).  Every plan converges, and a sample of
+    columns reaches its simplex optimum."""
+    c = cfg0
+    case, lp = c["case"], c["lp"]
+    rng = np.random.default_rng(300)
+    K = 300
+    W = np.column_stack([np.ones(K), np.ones(K), rng.uniform(0, 1, K),
+                         SC.W0_BOT * 10.0 ** (3 * rng.uniform(0, 1, K))])
+    b, l, u = L.bounds(lp, W)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    cs = make(lgk, case, 2)
+    res = lgk.solve_weightings(cs, W, rho, tol=5e-5, max_iter=30000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    for j in rng.choice(K, size=8, replace=False):
+        opt = SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj
+        assert abs(st["obj"][j] - opt) / max(1.0, abs(opt)) <= 1e-3, j
