@@ -866,7 +866,7 @@ int tc_gemm1_lo(ResultData& r, bool pdl, bool first_only) {
 }
 
 int tc_gemm2_lo(ResultData& r, bool pdl, bool first_only) {
-    if (r.wide)
+    if (r.plan2.mt == 2)
         return launch<1, 1, 1, true, EPI_STORE, 2>(r.maps.Alo_mn, r.maps.V, r.plan2, r, r.c2.p, pdl,
                                                    first_only);
     return launch<1, 1, 1, true, EPI_STORE>(r.maps.Alo_mn, r.maps.V, r.plan2, r, r.c2.p, pdl, first_only);
@@ -885,7 +885,7 @@ int tc_solve(ResultData& r, bool pdl) {
 
 int tc_gemm2(ResultData& r, bool pdl) {
     if (r.cs->na == 2 && !r.refine) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
-    if (r.wide) return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    if (r.plan2.mt == 2) return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
     return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
 }
 
