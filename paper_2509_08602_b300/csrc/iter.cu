@@ -158,7 +158,6 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
     }
 }
 
-// rhs = A R1 + q2 - 2 P2(q2).  Grid (m_pad / 128, Kp), 128 threads.
 // rhs = A R1 (+ the lagged lo R1) + q2 - 2 P2(q2), split into three BF16
 // parts (the solve amplifies input rounding).  Four rows per thread; grid
 // (m_pad / 256, Kp), 64 threads.
@@ -244,7 +243,7 @@ __global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, voi
 }
 
 // q1' = P1(q1) - c/rho - W and R1' = 2 P1(q1') - q1' - c/rho from W = A^T V;
-// residual partials of the n-block (one per 128-row tile and column).  The
+// residual partials of the n-block (one per 128-row block and column).  The
 // FP32 form's step after its cuBLAS GEMM2 (the BF16 forms run it in the
 // tensor-core GEMM2 epilogue).  Grid (n_pad / 128, Kp), 128 threads.
 template <bool BF16>

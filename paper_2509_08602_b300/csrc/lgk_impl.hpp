@@ -32,7 +32,7 @@ struct CaseData {
 
     // problem sizes (Appendix A): m = 24N + N rows, n = P + 8N columns
     int n_iso = 0, n_pts = 0, n_beams = 0, m = 0, n = 0;
-    int m_pad = 0, n_pad = 0;              // multiples of 128
+    int m_pad = 0, n_pad = 0;              // multiples of 256
     int n_targets = 0, n_oars = 0, n_slot = 0;
     double beta = 1.0;
     std::vector<int> slot_count;           // points per slot (TS/TI/R per target, LD1, LD2, OAR)

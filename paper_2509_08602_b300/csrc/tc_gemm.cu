@@ -3,25 +3,30 @@
 // swizzle, no multicast) through an mbarrier ring, warp-specialised CTA:
 //   warp 0      TMA producer (one elected lane)
 //   warp 1      TMEM allocator + MMA issuer (one elected lane)
-//   warps 2..9  epilogue: tcgen05.ld of the 128 x N accumulator, two warps per
-//               TMEM lane quarter (one row per thread, half the columns each)
+//   warps 2..9  epilogue: tcgen05.ld of the accumulators, two warps per TMEM
+//               lane quarter (one row per thread; the two warps take the two
+//               column halves of a 128-row tile, or the two 128-row halves of
+//               a 256-row tile)
 //
-// Output tile: 128 rows of the long dimension (m for GEMM1 and the solve, n
-// for GEMM2) x N columns (weightings, N <= 256).  The kernel is persistent and
-// stream-K scheduled: the (tile, 64-wide k block) units of a GEMM are cut into
-// one contiguous run per CTA, so every SM streams the same number of operand
-// blocks; a run is split into segments at tile boundaries, each segment's
-// partial sum goes to its own slot (two TMEM accumulators, so the epilogue of
-// one segment overlaps the loads and MMAs of the next), and the reduce kernels
-// add a tile's slots in k order (deterministic).  Each product A.B of the
-// iteration is a sum of BF16 x BF16 terms (exact products, FP32 sums):
-//   GEMM1   A . R1         = A_hi.R1_hi + A_hi.R1_lo + A_lo.R1_hi  (3 terms; the
-//                            one-term-A form drops A_lo: 2 terms)
+// Output tile: 128 or 256 rows (MT = 1, 2) of the long dimension (m for
+// GEMM1 and the solve, n for GEMM2) x N columns (weightings, N <= 256).  The
+// kernel is persistent and stream-K scheduled: the (tile, 64-wide k block)
+// units of a GEMM are cut into one contiguous run per CTA, so every SM
+// streams the same number of operand blocks; a run is split into segments at
+// tile boundaries, each segment's partial sum goes to its own slot (up to four
+// accumulator sets in TMEM, so the epilogue of one segment overlaps the loads
+// and MMAs of the next), and a tile's slots are added in k order
+// (deterministic).  Each product A.B is a sum of BF16 x BF16 terms (exact
+// products, FP32 sums):
+//   GEMM1   A . R1         = A_hi.R1_hi + A_hi.R1_lo + A_lo.R1_hi  (3 terms; with
+//                            the lagged low term, A_hi.R1 every iteration and
+//                            A_lo.R1_hi on the full ones; the one-term-A form
+//                            drops A_lo: 2 terms)
 //   solve   S^{-1} . rhs   = G_hi.r_hi + G_hi.r_mid + G_mid.r_hi
 //                            + G_hi.r_lo + G_mid.r_mid + G_lo.r_hi (6 terms;
 //                            S^{-1} and rhs each split into three BF16 parts,
 //                            because S amplifies the rounding of its input)
-//   GEMM2   A^T . V        = A_hi^T.V_hi + A_hi^T.V_lo + A_lo^T.V_hi (3 or 2 terms)
+//   GEMM2   A^T . V        = A_hi^T.V_hi + A_hi^T.V_lo + A_lo^T.V_hi (as GEMM1)
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -140,20 +145,6 @@ __device__ inline void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ inline void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -214,25 +205,21 @@ struct TcArgs {
     int out_ld;             // EPI_STORE: rows of the output matrix (m_pad or n_pad)
     int first_only;         // do the work only in the solve's first iteration (else return)
     float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
-    void* out;              // EPI_RHS: rhs [3][Kp][m_pad]; EPI_SOLVE: V [2][Kp][m_pad];
+    void* out;              // EPI_STORE: float [Kp][out_ld];
                             // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
 };
 
 // What a finished output tile becomes.  EPI_PARTIAL: every segment stores its
 // partial sum in its slot and a separate element-wise kernel adds a tile's
-// slots (GEMM1 and the solve: few output tiles, each split over ~6 CTAs, so
-// finishing them inside the GEMM would leave the summing to a handful of CTAs
-// at the end of the kernel).  Otherwise the element-wise step of the
-// iteration that consumes this GEMM's result is applied by the CTA that
-// completes the tile (GEMM2: ~2 tiles per CTA, most of them whole):
-//   EPI_RHS    rhs = A R1 + q2 - 2 P2(q2), split into three BF16 terms
-//   EPI_SOLVE  v = S^{-1} rhs: q2' = v + P2(q2), v split into two BF16 terms,
-//              residual partials of the m-block
+// slots (GEMM1 and the solve: few output tiles, each split over many CTAs,
+// so finishing them inside the GEMM would leave the summing to a handful of
+// CTAs at the end of the kernel).  Otherwise the CTA that completes a tile
+// sums its slots in k order and applies:
 //   EPI_Q1     W = A^T V: q1' = P1(q1) - c/rho - W, R1' = 2 P1(q1') - q1' - c/rho
 //              as two BF16 terms, residual partials of the n-block (W plus the
 //              lagged low-term product lo^T v when iterating with A_hi)
 //   EPI_STORE  the product as FP32 [Kp][out_ld] (the lagged low-term products)
-enum { EPI_RHS = 0, EPI_SOLVE = 1, EPI_Q1 = 2, EPI_PARTIAL = 3, EPI_STORE = 4 };
+enum { EPI_Q1 = 2, EPI_PARTIAL = 3, EPI_STORE = 4 };
 
 constexpr int kThreads = 320;               // 2 producer/MMA warps + 8 epilogue warps
 constexpr int kEpiThreads = 256;
@@ -300,58 +287,6 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
         float* o = static_cast<float*>(a.out) + (size_t)j0 * a.out_ld + row;
 #pragma unroll
         for (int c = 0; c < kChunk; ++c) o[(size_t)c * a.out_ld] = v[c];
-    } else if (EPI == EPI_RHS) {
-        const size_t plane = (size_t)cx.Kp * cx.m_pad;
-        const float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
-        float q[kChunk], wb[kChunk];
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            q[c] = q2p[(size_t)c * cx.m_pad];
-            wb[c] = __ldg(cx.wbot + j0 + c);
-        }
-        const bool tau_row = row >= cx.n_beams && row < cx.m;
-        const double dr = tau_row ? cx.Dr[row] : 0.0;
-        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
-            const float r = v[c] + q[c] - 2.f * fminf(q[c], bb);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(r);
-            const float r1 = r - __bfloat162float(hi);
-            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-            const size_t o = (size_t)c * cx.m_pad;
-            d[o] = hi;
-            d[plane + o] = mid;
-            d[2 * plane + o] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-        }
-    } else if (EPI == EPI_SOLVE) {
-        const size_t plane = (size_t)cx.Kp * cx.m_pad;
-        float* q2p = cx.q2 + (size_t)j0 * cx.m_pad + row;
-        float q[kChunk], wb[kChunk];
-        int act[kChunk];
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            q[c] = q2p[(size_t)c * cx.m_pad];
-            wb[c] = __ldg(cx.wbot + j0 + c);
-            act[c] = cx.active[j0 + c];
-        }
-        const bool tau_row = row >= cx.n_beams && row < cx.m;
-        const double dr = tau_row ? cx.Dr[row] : 0.0;
-        __nv_bfloat16* d = static_cast<__nv_bfloat16*>(a.out) + (size_t)j0 * cx.m_pad + row;
-#pragma unroll
-        for (int c = 0; c < kChunk; ++c) {
-            const float bb = tau_row ? (float)(wb[c] * dr) : 0.0f;
-            const float zo = fminf(q[c], bb), qn = v[c] + zo;
-            const size_t o = (size_t)c * cx.m_pad;
-            if (act[c]) q2p[o] = qn;
-            __nv_bfloat16 hi, lo;
-            split_bf16(v[c], hi, lo);
-            d[o] = hi;
-            d[plane + o] = lo;
-            const float yo = q[c] - zo, zn = fminf(qn, bb), yn = qn - zn;
-            const float r = yn - yo, x = qn - yo, s = zn - zo;
-            res[c][0] = r * r; res[c][1] = x * x; res[c][2] = zn * zn; res[c][3] = s * s; res[c][4] = yn * yn;
-        }
     } else {
         Q1In in;
         q1_load(cx, row, j0, in);
@@ -359,9 +294,10 @@ __device__ inline void epi_op(const IterCtx& cx, const TcArgs& a, int row, int j
     }
 }
 
-// Reduce the residual terms of kChunk columns over the 128 rows (the 4 warps
-// of one column half `hf`) and store them as this tile's partial for those
-// columns.  Both halves call it the same number of times (barriers).
+// Reduce the residual terms of kChunk columns over 128 rows (the 4 warps of
+// group `hf`: one column half of a 128-row tile, or one 128-row half of a
+// 256-row tile) and store them as that 128-row block's partial for those
+// columns.  Both groups call it the same number of times (barriers).
 __device__ inline void epi_resid(float res[kChunk][5], float* red, double* dst, int lane, int ew, int hf,
                                  int et) {
 #pragma unroll
@@ -524,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int hrow = MT == 2 ? hf : 0;              // this warp's 128-row sub-tile
         const int half = a.n_tile / 2;                  // multiple of kChunk
         const int cbeg = MT == 2 ? 0 : hf * half, cend = MT == 2 ? a.n_tile : cbeg + half;
-        const bool check = (EPI == EPI_SOLVE || EPI == EPI_Q1) && is_check_iter(ctrl, cx.check_every, cx.tol);
+        const bool check = EPI == EPI_Q1 && is_check_iter(ctrl, cx.check_every, cx.tol);
         bool ok = true;
         for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
             const int b = u % NBUF;
@@ -534,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int sb = a.tile_begin[tile], se = a.tile_begin[tile + 1];
             const int row = (rt * MT + hrow) * 128 + r, col0 = ct * a.n_tile;
             double* rdst = cx.resid +
-                           ((size_t)((EPI == EPI_SOLVE ? cx.n_resid_n : 0) + rt * MT + hrow) * cx.Kp + col0) * 5;
+                           ((size_t)(rt * MT + hrow) * cx.Kp + col0) * 5;
             if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
             tc_fence_after();
             const uint32_t base =
