@@ -3,13 +3,14 @@
 Precision forms: 0 = FP32 (cuBLAS comparison form), 1 = BF16 (A rounded to
 one BF16 term), 2 = BF16X3 (A as two BF16 terms; the product form).
 
-Tolerances (derived in DESIGN.md, "Tolerances"):
+Tolerances:
   * one iteration from a common state, element by element on the same LP (the
     matrix each form actually iterates on: FP32-rounded, BF16-rounded, or the
     two-term BF16 sum): max |gpu - oracle| <= ||A||_2^2 u max |q| with
     u = 2^-17 for the BF16 forms (iterates split into two BF16 terms) and
-    u = 2^-24 sqrt(n) for FP32 (FP32 sums of n terms); S^{-1} has norm <= 1
-    since S = I + A A^T;
+    u = 2^-24 sqrt(n) for FP32 (FP32 sums of n terms): the GEMMs see
+    relative input rounding u, A and A^T each scale it by ||A||_2, and
+    S^{-1} has norm <= 1 since S = I + A A^T;
   * converged plans (tol 1e-4) of the FP32 and BF16X3 forms against the FP64
     oracle on the exact matrix: |obj - obj*| / max(1, |obj*|) <= 1e-3 against
     the simplex optimum, relative primal/dual residual <= 1e-4, coverage,
