@@ -71,6 +71,15 @@ def test_default_params(lgk):
     assert p.lo_refresh_iters == 8000
 
 
+def test_create_case_rejects_bad_params(lgk):
+    phi, kind, sid = _tiny()
+    for kw in (dict(lo_refresh=3), dict(lo_refresh_iters=-1), dict(check_every=0), dict(precision=7)):
+        with pytest.raises(lgk.LgkError) as e:
+            lgk.create_case(phi, kind, sid, 1, [20.0], [1.0], [1.0], 10.0, 5.0, 3.0,
+                            params=lgk.default_params(**kw))
+        assert e.value.code == 1, kw
+
+
 def test_null_arguments_are_errors_not_crashes(lgk):
     lib = lgk._lib
     h = ctypes.c_void_p()
