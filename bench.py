@@ -307,9 +307,16 @@ def run_ours(args, rank, world, local):
                          params=params)
     rule = dict(w0_bot=SC.W0_BOT, rho0=RHO0_PER_BETA * cs.beta, tol=args.tol,
                 max_iter=args.max_iter)
+    sw = args.stream_width
+    if sw:
+        # streaming: the slowest weightings (lowest BOT weight) enter first
+        W = W[np.argsort(W[:, 3], kind="stable")]
+    k_launch = min(sw, K) if sw else K         # columns one GEMM launch carries
     for _ in range(args.warmup):
-        r = lgk.solve_weightings(cs, W, None, **rule)
-        r.close()
+        if sw:
+            lgk.solve_stream(cs, W, None, width=sw, **rule)
+        else:
+            lgk.solve_weightings(cs, W, None, **rule).close()
     lgk.launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -324,14 +331,18 @@ def run_ours(args, rank, world, local):
     r_last = None
     for _ in range(args.steps):
         t1 = time.perf_counter()
-        r = lgk.solve_weightings(cs, W, None, **rule)
-        lat.append(time.perf_counter() - t1)
-        st = lgk.fetch_stats(r)
+        if sw:
+            st = lgk.solve_stream(cs, W, None, width=sw, **rule)
+            lat.append(time.perf_counter() - t1)
+        else:
+            r = lgk.solve_weightings(cs, W, None, **rule)
+            lat.append(time.perf_counter() - t1)
+            st = lgk.fetch_stats(r)
+            if r_last is not None:
+                r_last.close()
+            r_last = r
         conv += int(st["converged"].sum())
         iters.append(st["iters"])
-        if r_last is not None:
-            r_last.close()
-        r_last = r
     ev1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -352,12 +363,17 @@ def run_ours(args, rank, world, local):
                            case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                            params=lgk.default_params(precision=prec, device=local, profile=1,
                                                      lo_refresh=int(refine), check_every=args.check_every))
-    r = lgk.solve_weightings(cs_p, W, None, **rule)
-    for k, (ms, nl) in lgk.fetch_profile(r).items():
+    if sw:
+        pr = lgk.solve_stream(cs_p, W, None, width=sw, profile=True, **rule)["profile"]
+        prof_iters = pr["gemm1"][1]          # iterations of the whole stream (one GEMM1 each)
+    else:
+        r = lgk.solve_weightings(cs_p, W, None, **rule)
+        pr = lgk.fetch_profile(r)
+        prof_iters = int(lgk.fetch_stats(r)["iters"].max())
+        r.close()
+    for k, (ms, nl) in pr.items():
         prof[k][0] += ms
         prof[k][1] += nl
-    prof_iters = int(lgk.fetch_stats(r)["iters"].max())
-    r.close()
     cs_p.close()
 
     # e2e: pinned host inputs, create + solve + fetch per step
@@ -373,10 +389,15 @@ def run_ours(args, rank, world, local):
                              params=lgk.default_params(precision=prec, device=local,
                                                        lo_refresh=int(refine),
                                                        check_every=args.check_every))
-        r = lgk.solve_weightings(c2, W, None, **rule)
-        t, tau = lgk.fetch_times(r)
-        conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
-        r.close()
+        if sw:
+            s2 = lgk.solve_stream(c2, W, None, width=sw, **rule)
+            t, tau = s2["t"], s2["tau"]
+            conv_e2e += int(s2["converged"].sum())
+        else:
+            r = lgk.solve_weightings(c2, W, None, **rule)
+            t, tau = lgk.fetch_times(r)
+            conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
+            r.close()
         c2.close()
     torch.cuda.synchronize()
     e2e_s = allreduce_max(time.perf_counter() - t0, world)
@@ -412,7 +433,7 @@ def run_ours(args, rank, world, local):
         m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
         dom = max(prof, key=lambda k: prof[k][0])
         ms_avg = prof[dom][0] / max(prof[dom][1], 1)
-        nbytes, flops, executed, xbytes = kernel_work(dom, m, n, K, args.precision, refine)
+        nbytes, flops, executed, xbytes = kernel_work(dom, m, n, k_launch, args.precision, refine)
         t_hbm = xbytes / (hbm * 1e9)
         t_tensor = executed / (tf_sus * 1e12)
         if t_hbm >= t_tensor:
@@ -438,11 +459,15 @@ def run_ours(args, rank, world, local):
         roof["kernel_share"] = {k: round(v[0] / total_ms, 4) for k, v in prof.items()}
         roof["timing"] = (f"CUDA events around every kernel of one profiled solve of the same batch "
                           f"({prof_iters} iterations); the timed steps run without them")
-        roof["us_per_iteration_timed"] = t_max / args.steps / max_iters * 1e6
+        # iterations per step: the batch runs until its slowest column stops;
+        # a stream's count is that of its profiled run (the same schedule)
+        roof["us_per_iteration_timed"] = t_max / args.steps / (prof_iters if sw else max_iters) * 1e6
         roof["us_per_iteration_profiled"] = total_ms / prof_iters * 1e3
         cpu = None
         if not args.no_cpu_baseline:
             cpu = oracle_sample(case, W, mean_iters)
+        if not args.no_extras and r_last is None:     # streaming: one batch solve for the extras
+            r_last = lgk.solve_weightings(cs, W, None, **rule)
         extra = {} if args.no_extras else {
             "plan_metrics": bench_metrics(lgk, case, r_last),
             "two_pass": bench_two_pass(lgk, case, W, args, local)}
@@ -455,6 +480,9 @@ def run_ours(args, rank, world, local):
                "e2e": {"value": e2e_value, "unit": "plans/s", "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h),
                        "note": "create_case from pinned host phi + solve + fetch_times"},
+               "batching": (f"stream: {K} weightings through {sw} columns, each column refilled "
+                            "with the next weighting (ascending w_BOT) when it stops" if sw else
+                            f"one batch of {K} columns, run until every column stops"),
                "gpu_launches": int(launches),
                "clocks": clk, "roofline": roof, "cpu_baseline": cpu,
                "latency_ms": {"p50": lat_ms[len(lat_ms) // 2],
@@ -463,7 +491,8 @@ def run_ours(args, rank, world, local):
                "converged_fraction": conv / (K * args.steps),
                "fp32_form": fp32, **extra}
         print(json.dumps(out), flush=True)
-    r_last.close()
+    if r_last is not None:
+        r_last.close()
     cs.close()
     return 0
 
@@ -656,6 +685,9 @@ def main():
                     help="iterations between residual tests (and low-term refreshes)")
     ap.add_argument("--exact", action="store_true",
                     help="both BF16 terms of A in every iteration (lo_refresh = 0)")
+    ap.add_argument("--stream-width", type=int, default=32,
+                    help="streaming solve: the workload's weightings through this many columns, "
+                         "refilled as columns stop; 0: one batch of all weightings")
     ap.add_argument("--precision", default="bf16x3", choices=sorted(PRECISIONS),
                     help="BF16 form of A: bf16x3 (two BF16 terms; the plans match FP64), bf16 (one term)")
     ap.add_argument("--no-extras", action="store_true",

@@ -262,6 +262,40 @@ int lgk_solve_weightings_masked(lgk_case* cs, int K, const double* W, const doub
                                 const uint32_t* mask, const double* q1_init, const double* q2_init,
                                 lgk_result** out);
 
+/*
+ * lgk_solve_stream -- K_total weightings through `width` columns of one
+ * resident case (continuous batching of a weighting set).  The first
+ * min(width, K_total) weightings start together; whenever a column stops
+ * (its residual test passes, or it has run max_iter iterations of its own),
+ * its results are copied out at the next graph boundary (every 5 residual-
+ * test intervals) and the next weighting, in the given order, takes the
+ * column from q = 0.  Columns never interact, so each weighting runs the
+ * iteration of lgk_solve_weightings (Eq. admm) from its own start; only
+ * the lagged low term's refresh points fall at different iterations of its
+ * trajectory (the fixed point is unchanged), and a refilled column's first
+ * iterations before its first residual test add no low-term product.
+ * A batch's time is set by its slowest column while every iteration streams
+ * all of A for every column; refilling lets a set of weightings larger than
+ * the batch width run at the cost of the mean iteration count instead.
+ *   W:   K_total x 4 host array (w_T, w_R, w_LD, w_BOT), admitted in order.
+ *   rho: K_total host array, or NULL for Eq. rho_rule (w0_bot, rho0 as in
+ *        lgk_solve_weightings).
+ *   max_iter: per weighting; a column is stopped within one graph replay
+ *        (5 x check_every iterations) after reaching it.
+ *   width: columns iterated at once, 1 <= width <= 4096.
+ * Outputs (host arrays, each may be NULL), per weighting in input order:
+ *   t (K_total x 24N), tau (K_total x N): as lgk_fetch_times;
+ *   iters, obj, rel_pri, rel_dual, converged (K_total): as lgk_fetch_stats;
+ *   prof_ms, prof_launches (LGK_K_COUNT): per-kernel CUDA-event time and
+ *        launches as lgk_fetch_profile (only with lgk_params.profile = 1).
+ * 1 <= K_total <= 1 << 20.  LGK_EINVAL on bad arguments; on any error the
+ * outputs are undefined.
+ */
+int lgk_solve_stream(lgk_case* cs, int K_total, const double* W, const double* rho, double w0_bot,
+                     double rho0, double tol, int max_iter, int width, double* t, double* tau, int* iters,
+                     double* obj, double* rel_pri, double* rel_dual, uint8_t* converged, double* prof_ms,
+                     long long* prof_launches);
+
 /* ------------------------------------------------------------------------
  * Two-pass optimisation (Sec. 2.C).  The first pass takes its low-dose
  * points from a geometric expansion of the targets; the second takes them,

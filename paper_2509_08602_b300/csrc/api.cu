@@ -153,6 +153,24 @@ int lgk_case_info(const lgk_case* c, int* m, int* n, double* beta, size_t* bytes
     return LGK_OK;
 }
 
+// Per-weighting penalties: the caller's, or Eq. rho_rule.
+static int column_rho(int K, const double* W, const double* rho, double w0_bot, double rho0,
+                      std::vector<double>& r) {
+    r.assign(K, 0.0);
+    if (rho) {
+        if (!finite_pos(rho, K)) return fail(LGK_EINVAL, "rho must be finite and > 0");
+        r.assign(rho, rho + K);
+        return LGK_OK;
+    }
+    if (!(w0_bot > 0) || !(rho0 > 0) || !isfinite(w0_bot) || !isfinite(rho0))
+        return fail(LGK_EINVAL, "rho rule needs w0_bot > 0 and rho0 > 0");
+    for (int j = 0; j < K; ++j) {
+        if (!(W[4 * (size_t)j + 3] > 0)) return fail(LGK_EINVAL, "rho rule needs w_BOT > 0");
+        r[j] = rho0 * sqrt(w0_bot / W[4 * (size_t)j + 3]);     // Eq. rho_rule
+    }
+    return LGK_OK;
+}
+
 int lgk_solve_weightings_masked(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
                                 double rho0, double tol, int max_iter, const uint32_t* mask,
                                 const double* q1_init, const double* q2_init, lgk_result** out) {
@@ -162,18 +180,9 @@ int lgk_solve_weightings_masked(lgk_case* c, int K, const double* W, const doubl
     if (K < 1 || K > 4096) return fail(LGK_EINVAL, "need 1 <= K <= 4096");
     if (!finite_nonneg(W, (size_t)K * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
     if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
-    std::vector<double> r(K);
-    if (rho) {
-        if (!finite_pos(rho, K)) return fail(LGK_EINVAL, "rho must be finite and > 0");
-        r.assign(rho, rho + K);
-    } else {
-        if (!(w0_bot > 0) || !(rho0 > 0) || !isfinite(w0_bot) || !isfinite(rho0))
-            return fail(LGK_EINVAL, "rho rule needs w0_bot > 0 and rho0 > 0");
-        for (int j = 0; j < K; ++j) {
-            if (!(W[4 * j + 3] > 0)) return fail(LGK_EINVAL, "rho rule needs w_BOT > 0");
-            r[j] = rho0 * sqrt(w0_bot / W[4 * j + 3]);     // Eq. rho_rule
-        }
-    }
+    std::vector<double> r;
+    int rrc = column_rho(K, W, rho, w0_bot, rho0, r);
+    if (rrc) return rrc;
     LGK_CUDA_TRY(cudaSetDevice(c->d->device));
     std::unique_ptr<ResultData> res;
     try {
@@ -213,6 +222,56 @@ int lgk_solve_weightings(lgk_case* c, int K, const double* W, const double* rho,
                          double rho0, double tol, int max_iter, lgk_result** out) {
     return lgk_solve_weightings_masked(c, K, W, rho, w0_bot, rho0, tol, max_iter, nullptr, nullptr,
                                        nullptr, out);
+}
+
+int lgk_solve_stream(lgk_case* c, int K_total, const double* W, const double* rho, double w0_bot,
+                     double rho0, double tol, int max_iter, int width, double* t, double* tau, int* iters,
+                     double* obj, double* rel_pri, double* rel_dual, uint8_t* converged, double* prof_ms,
+                     long long* prof_launches) {
+    if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
+    if (K_total < 1 || K_total > (1 << 20) || width < 1 || width > 4096)
+        return fail(LGK_EINVAL, "need 1 <= K_total <= 2^20 and 1 <= width <= 4096");
+    if (!finite_nonneg(W, (size_t)K_total * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
+    if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
+    if ((prof_ms || prof_launches) && !c->d->prm.profile)
+        return fail(LGK_EINVAL, "profile outputs need lgk_params.profile = 1");
+    std::vector<double> r;
+    int rc = column_rho(K_total, W, rho, w0_bot, rho0, r);
+    if (rc) return rc;
+    LGK_CUDA_TRY(cudaSetDevice(c->d->device));
+    std::unique_ptr<ResultData> res;
+    try {
+        res.reset(new ResultData);
+    } catch (const std::bad_alloc&) {
+        return fail(LGK_ENOMEM, "host allocation failed");
+    }
+    res->cs = c->d;
+    res->K = std::min(width, K_total);
+    res->tol = tol;
+    res->max_iter = 1 << 30;        // the device never stops a column on its count; the host does
+    StreamSpec ss;
+    ss.K_total = K_total;
+    ss.W = W;
+    ss.rho = r.data();
+    ss.max_iter = max_iter;
+    ss.t = t;
+    ss.tau = tau;
+    ss.iters = iters;
+    ss.obj = obj;
+    ss.rel_pri = rel_pri;
+    ss.rel_dual = rel_dual;
+    ss.converged = converged;
+    try {
+        rc = run_solve(*res, W, r.data(), nullptr, nullptr, nullptr, &ss);
+    } catch (const std::bad_alloc&) {
+        rc = fail(LGK_ENOMEM, "host allocation failed");
+    }
+    if (rc) return rc;
+    for (int k = 0; k < LGK_K_COUNT; ++k) {
+        if (prof_ms) prof_ms[k] = res->prof_ms[k];
+        if (prof_launches) prof_launches[k] = res->prof_n[k];
+    }
+    return LGK_OK;
 }
 
 int lgk_fetch_times(const lgk_result* r, double* t, double* tau) {

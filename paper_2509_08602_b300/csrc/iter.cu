@@ -111,11 +111,6 @@ __device__ inline float4 gemm_out4(const SumSrc& s, int i, int j) {
 
 __device__ inline float f4(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 
-// Element-wise kernels over the m-block (one element per thread, grid
-// (m_pad / 256, Kp)) or the n-block; kCols is the column group of the
-// residual partials written per 128-row tile.
-constexpr int kCols = 8;
-
 __device__ inline void block_sum5(float v[5], double* out) {
     __shared__ float red[5][8];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -380,6 +375,45 @@ __global__ void k_lambda(IterCtx cx, int K, double* lam) {
     lam[(size_t)j * cx.m + i] = cx.Dr[i] * (double)cx.rho[j] * fmax(q - bb, 0.0);
 }
 
+// lambda (as k_lambda) of the listed columns: lam[c][m] for column cols[c].
+__global__ void k_lambda_cols(IterCtx cx, const int* __restrict__ cols, double* lam) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+    if (i >= cx.m) return;
+    const int j = cols[c];
+    const double q = cx.q2[(size_t)j * cx.m_pad + i];
+    const double bb = (double)b_of(i, j, cx.n_beams, cx.m, cx.Dr, cx.wbot);
+    lam[(size_t)c * cx.m + i] = cx.Dr[i] * (double)cx.rho[j] * fmax(q - bb, 0.0);
+}
+
+// A column taken by a new weighting (streaming solve): q1 = q2 = 0, R1 from
+// q1 = 0 under the column's new bounds (as k_init_r1), lagged low-term
+// products zero until the column's first full iteration.
+template <bool BF16>
+__global__ void k_reset_cols(IterCtx cx, const int* __restrict__ cols, void* R1, float* c1, float* c2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, j = cols[blockIdx.y];
+    if (e < cx.n_pad) {
+        const size_t o = (size_t)j * cx.n_pad + e;
+        const int sl = cx.col_slot[e];
+        const float u = u_at(cx, e, sl, j);
+        const float r = 2.f * fminf(0.f, u) - cx.c_slot[sl] * cx.inv_rho[j];
+        cx.q1[o] = 0.f;
+        if (BF16) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(r, hi, lo);
+            static_cast<__nv_bfloat16*>(R1)[o] = hi;
+            static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
+        } else {
+            static_cast<float*>(R1)[o] = r;
+        }
+        if (c2) c2[o] = 0.f;
+    }
+    if (e < cx.m_pad) {
+        const size_t o = (size_t)j * cx.m_pad + e;
+        cx.q2[o] = 0.f;
+        if (c1) c1[o] = 0.f;
+    }
+}
+
 // q1 (K x n) and q2 (K x m) of the q-form state, FP64.
 __global__ void k_state(IterCtx cx, int K, double* q1, double* q2) {
     int e = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -523,7 +557,7 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
 }
 
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init, const uint32_t* mask) {
+              const double* q2_init, const uint32_t* mask, const StreamSpec* stream) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
     const bool bf16 = cs.prm.precision != LGK_PREC_FP32;
@@ -561,10 +595,11 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
 
     // per-column tables (Appendix A bounds; Eq. rho_rule or caller rho)
     std::vector<float> utab((size_t)Kp * S + S, 0.0f), colp((size_t)4 * Kp, 0.0f);
-    for (int j = 0; j < K; ++j) {
-        double wT = W[4 * j], wR = W[4 * j + 1], wLD = W[4 * j + 2], wB = W[4 * j + 3];
+    // column j's tables for weights w = (w_T, w_R, w_LD, w_BOT), penalty rh and
+    // per-slot point counts nc
+    auto fill_col = [&](int j, const double* w, double rh, const int* nc) {
+        const double wT = w[0], wR = w[1], wLD = w[2], wB = w[3];
         float* u = &utab[(size_t)j * S];
-        const int* nc = &cnt[(size_t)j * S];
         for (int k = 0; k < T; ++k) {
             u[3 * k] = nc[3 * k] ? (float)(cs.q_area[k] * wT / nc[3 * k]) : 0.f;
             u[3 * k + 1] = nc[3 * k + 1] ? (float)(cs.q_vol[k] * wT / nc[3 * k + 1]) : 0.f;
@@ -575,10 +610,11 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         u[slot_oar(T)] = INFINITY;
         u[slot_bot(T)] = INFINITY;
         u[slot_pad(T)] = 0.f;
-        colp[j] = (float)rho[j];
-        colp[Kp + j] = (float)(1.0 / rho[j]);
+        colp[j] = (float)rh;
+        colp[Kp + j] = (float)(1.0 / rh);
         colp[2 * Kp + j] = (float)wB;
-    }
+    };
+    for (int j = 0; j < K; ++j) fill_col(j, W + 4 * (size_t)j, rho[j], &cnt[(size_t)j * S]);
     for (int s = 0; s < S; ++s) utab[(size_t)Kp * S + s] = cs.c_of_slot[s];
 
     // buffers
@@ -603,6 +639,17 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.n_resid_m = cs.m_pad / 128;
     if ((rc = r.resid.alloc((size_t)(r.n_resid_n + r.n_resid_m) * Kp * 5 * 8))) return rc;
     if ((rc = r.stats.alloc((size_t)3 * Kp * 8))) return rc;
+    // streaming: the weighting each column holds (-1: none), the iteration
+    // it started at, the next weighting to admit
+    std::vector<int> w_of, start_it;
+    int next_w = K;
+    DevBuf cols_d, lam_d;
+    if (stream) {
+        w_of.assign(Kp, -1);
+        start_it.assign(Kp, 0);
+        for (int j = 0; j < K; ++j) w_of[j] = j;
+        if ((rc = cols_d.alloc((size_t)Kp * 4)) || (rc = lam_d.alloc((size_t)Kp * cs.m * 8))) return rc;
+    }
 
     std::vector<int> act(2 * Kp, 0);
     for (int j = 0; j < K; ++j) act[j] = 1;
@@ -703,6 +750,87 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
 
     Control* hc = nullptr;
     LGK_CUDA_TRY(cudaMallocHost(&hc, sizeof(Control)));
+    // streaming, at a replay boundary (the device idle): copy out the results
+    // of the columns that stopped (their test passed, or their own iteration
+    // cap), give those columns the next weightings, and push the new flags,
+    // tables and counters.  done: no column holds a weighting; age: the
+    // iterations of the oldest running column.
+    auto stream_boundary = [&](bool& done, int& age) -> int {
+        const StreamSpec& ss = *stream;
+        std::vector<int> a(2 * (size_t)Kp), its(Kp);
+        LGK_CUDA_TRY(cudaMemcpyAsync(a.data(), r.active.p, a.size() * 4, cudaMemcpyDeviceToHost, st));
+        LGK_CUDA_TRY(cudaMemcpyAsync(its.data(), r.iters.p, its.size() * 4, cudaMemcpyDeviceToHost, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int> ret;
+        for (int j = 0; j < Kp; ++j) {
+            if (w_of[j] < 0) continue;
+            if (a[j] && hc->iter - start_it[j] >= ss.max_iter) a[j] = 0;
+            if (!a[j]) ret.push_back(j);
+        }
+        if (!ret.empty()) {
+            k_objective<<<Kp, 256, 0, st>>>(cx, r.stats.as<double>() + 2 * Kp);
+            LGK_LAUNCH_CHECK();
+            LGK_CUDA_TRY(cudaMemcpyAsync(cols_d.p, ret.data(), ret.size() * 4, cudaMemcpyHostToDevice, st));
+            k_lambda_cols<<<dim3((cs.m + 255) / 256, (unsigned)ret.size()), 256, 0, st>>>(
+                cx, cols_d.as<int>(), lam_d.as<double>());
+            LGK_LAUNCH_CHECK();
+            std::vector<double> stv(3 * (size_t)Kp), lam(ret.size() * (size_t)cs.m);
+            LGK_CUDA_TRY(cudaMemcpyAsync(stv.data(), r.stats.p, stv.size() * 8, cudaMemcpyDeviceToHost, st));
+            LGK_CUDA_TRY(cudaMemcpyAsync(lam.data(), lam_d.p, lam.size() * 8, cudaMemcpyDeviceToHost, st));
+            LGK_CUDA_TRY(cudaStreamSynchronize(st));
+            // graph slots assume replays that start on a multiple of their
+            // length; the counter stops early only once no column runs
+            hc->iter = (int)round_up(hc->iter, per_graph);
+            std::vector<int> fill;
+            for (size_t c = 0; c < ret.size(); ++c) {
+                const int j = ret[c], w = w_of[j];
+                if (ss.iters) ss.iters[w] = its[j] - start_it[j];
+                if (ss.obj) ss.obj[w] = stv[2 * (size_t)Kp + j];
+                if (ss.rel_pri) ss.rel_pri[w] = stv[j];
+                if (ss.rel_dual) ss.rel_dual[w] = stv[(size_t)Kp + j];
+                if (ss.converged) ss.converged[w] = (uint8_t)(a[(size_t)Kp + j] != 0);
+                const double* l = &lam[c * (size_t)cs.m];
+                if (ss.t) std::copy(l, l + cs.n_beams, ss.t + (size_t)w * cs.n_beams);
+                if (ss.tau) std::copy(l + cs.n_beams, l + cs.m, ss.tau + (size_t)w * cs.n_iso);
+                w_of[j] = -1;
+                if (next_w < ss.K_total) {
+                    w_of[j] = next_w;
+                    start_it[j] = hc->iter;
+                    fill_col(j, ss.W + 4 * (size_t)next_w, ss.rho[next_w], cs.slot_count.data());
+                    a[j] = 1;
+                    a[(size_t)Kp + j] = 0;
+                    fill.push_back(j);
+                    ++next_w;
+                }
+            }
+            if (!fill.empty()) {
+                LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
+                LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
+                LGK_CUDA_TRY(cudaMemcpyAsync(cols_d.p, fill.data(), fill.size() * 4, cudaMemcpyHostToDevice, st));
+                const int ne = std::max(cs.n_pad, cs.m_pad);
+                dim3 g((ne + 255) / 256, (unsigned)fill.size());
+                float* c1 = r.refine ? r.c1.as<float>() : nullptr;
+                float* c2 = r.refine ? r.c2.as<float>() : nullptr;
+                if (bf16) k_reset_cols<true><<<g, 256, 0, st>>>(cx, cols_d.as<int>(), r.R1.p, c1, c2);
+                else k_reset_cols<false><<<g, 256, 0, st>>>(cx, cols_d.as<int>(), r.R1.p, c1, c2);
+                LGK_LAUNCH_CHECK();
+            }
+            int n_act = 0;
+            for (int j = 0; j < Kp; ++j) n_act += a[j] != 0;
+            hc->n_active = n_act;
+            LGK_CUDA_TRY(cudaMemcpyAsync(r.active.p, a.data(), a.size() * 4, cudaMemcpyHostToDevice, st));
+            LGK_CUDA_TRY(cudaMemcpyAsync(r.ctrl.p, hc, sizeof(Control), cudaMemcpyHostToDevice, st));
+            LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        done = true;
+        age = 0;
+        for (int j = 0; j < Kp; ++j)
+            if (w_of[j] >= 0) {
+                done = false;
+                age = std::max(age, hc->iter - start_it[j]);
+            }
+        return LGK_OK;
+    };
     int iter_before = 0;
     auto t0 = std::chrono::steady_clock::now();
     rc = LGK_OK;
@@ -745,8 +873,16 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
                 }
         }
         iter_before = hc->iter;
-        if (hc->n_active == 0) break;
-        if (r.refine && cs.prm.lo_refresh_iters > 0 && hc->iter >= cs.prm.lo_refresh_iters) {
+        int age = hc->iter;         // iterations of the oldest running column
+        if (stream) {
+            bool done = false;
+            if ((rc = stream_boundary(done, age))) break;
+            if (done) break;
+            iter_before = hc->iter;
+        } else if (hc->n_active == 0) {
+            break;
+        }
+        if (r.refine && cs.prm.lo_refresh_iters > 0 && age >= cs.prm.lo_refresh_iters) {
             // columns still running this long: continue with the literal
             // iteration (all terms every step) from the current state
             cudaGraphExecDestroy(r.graph);

@@ -115,9 +115,22 @@ struct ResultData {
 // set-up (setup.cu)
 int setup_case(CaseData& cs, const lgk_case_desc& d);
 
-// one solve (iter.cu)
+// Streaming solve (lgk_solve_stream): K_total weightings admitted into the
+// columns of one solve as earlier ones stop; results are written per
+// weighting (host arrays, each may be null).
+struct StreamSpec {
+    int K_total = 0;
+    const double* W = nullptr;       // K_total x 4
+    const double* rho = nullptr;     // K_total
+    int max_iter = 0;                // per weighting
+    double *t = nullptr, *tau = nullptr, *obj = nullptr, *rel_pri = nullptr, *rel_dual = nullptr;
+    int* iters = nullptr;
+    uint8_t* converged = nullptr;
+};
+
+// one solve (iter.cu); with `stream`, W and rho hold its first r.K weightings
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init, const uint32_t* mask);
+              const double* q2_init, const uint32_t* mask, const StreamSpec* stream = nullptr);
 int fetch_times(const ResultData& r, double* t, double* tau);
 int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double* dose);
 int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri,

@@ -222,7 +222,6 @@ struct TcArgs {
 enum { EPI_Q1 = 2, EPI_PARTIAL = 3, EPI_STORE = 4 };
 
 constexpr int kThreads = 320;               // 2 producer/MMA warps + 8 epilogue warps
-constexpr int kEpiThreads = 256;
 constexpr int kChunk = 8;                   // columns per epilogue step
 static_assert(32 % kChunk == 0, "a chunk's columns must share one point-selection word");
 constexpr int kABytes = 128 * 64 * 2;       // one 128 x 64 BF16 operand tile

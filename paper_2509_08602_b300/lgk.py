@@ -86,6 +86,11 @@ def _load():
                                                 C.c_double, C.c_double, C.c_double, C.c_int,
                                                 P(C.c_uint32), P(C.c_double), P(C.c_double),
                                                 P(C.c_void_p)]
+    lib.lgk_solve_stream.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double), C.c_double,
+                                     C.c_double, C.c_double, C.c_int, C.c_int, P(C.c_double),
+                                     P(C.c_double), P(C.c_int), P(C.c_double), P(C.c_double),
+                                     P(C.c_double), P(C.c_uint8), P(C.c_double), P(C.c_longlong)]
+    lib.lgk_solve_stream.restype = C.c_int
     lib.lgk_low_dose_volumes.argtypes = [C.c_void_p, P(C.c_double), C.c_int, C.c_int, P(C.c_double),
                                          P(C.c_double), P(C.c_uint32), P(C.c_int)]
     lib.lgk_sample_low_dose.argtypes = [C.c_int, C.c_int, P(C.c_uint32), P(C.c_int), C.c_uint64,
@@ -223,6 +228,38 @@ def solve_weightings(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: floa
                                      float(w0_bot), float(rho0), float(tol), int(max_iter),
                                      C.byref(h)))
     return Result(h, K, case)
+
+
+def solve_stream(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 0.0,
+                 tol: float = 1e-4, max_iter: int = 10000, width: int = 32,
+                 profile: bool = False) -> dict:
+    """lgk_solve_stream: the K_total weightings of W run through `width`
+    columns, each freed column taking the next weighting.  Returns, per
+    weighting in W's order, t (K_total x 24N), tau (K_total x N), iters, obj,
+    rel_pri, rel_dual, converged; with profile=True (the case created with
+    profile=1) also {kernel: (ms, launches)} under "profile"."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    if W.shape[1] != 4:
+        raise LgkError(1, "W must be K x 4")
+    K = W.shape[0]
+    r = None if rho is None else np.ascontiguousarray(np.broadcast_to(rho, (K,)), dtype=np.float64)
+    n_iso = case.m // 25
+    t = np.empty((K, 24 * n_iso))
+    tau = np.empty((K, n_iso))
+    it = np.empty(K, np.int32)
+    obj, rp, rd = np.empty(K), np.empty(K), np.empty(K)
+    conv = np.empty(K, np.uint8)
+    ms = np.zeros(len(KERNELS)) if profile else None
+    nl = np.zeros(len(KERNELS), np.int64) if profile else None
+    _check(_lib.lgk_solve_stream(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double), float(w0_bot),
+                                 float(rho0), float(tol), int(max_iter), int(width), _ptr(t, C.c_double),
+                                 _ptr(tau, C.c_double), _ptr(it, C.c_int), _ptr(obj, C.c_double),
+                                 _ptr(rp, C.c_double), _ptr(rd, C.c_double), _ptr(conv, C.c_uint8),
+                                 _ptr(ms, C.c_double), _ptr(nl, C.c_longlong)))
+    out = dict(t=t, tau=tau, iters=it, obj=obj, rel_pri=rp, rel_dual=rd, converged=conv.astype(bool))
+    if profile:
+        out["profile"] = {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNELS)}
+    return out
 
 
 def solve_weightings_warm(case: Case, W, rho=None, *, q1_init=None, q2_init=None,

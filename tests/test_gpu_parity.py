@@ -394,3 +394,42 @@ def test_wide_batch_two_column_tiles(lgk, cfg0):
     for j in rng.choice(K, size=8, replace=False):
         opt = SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj
         assert abs(st["obj"][j] - opt) / max(1.0, abs(opt)) <= 1e-3, j
+
+
+def test_stream_refills_columns_and_matches_the_batch(lgk, cfg0):
+    """Streaming solve: the 9 weightings through 4 columns (5 refills).
+    Every weighting converges to its simplex optimum (gap <= 1e-3) with
+    relative residuals <= 1e-4, its plan's metrics are within 0.5 % of the
+    oracle plan's (the batch parity bar), and its iteration count is the
+    batch solve's up to the shifted low-term refresh points."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    rule = dict(w0_bot=SC.W0_BOT, rho0=L.rho0_for(c["lp"]), tol=TOL, max_iter=20000)
+    s = lgk.solve_stream(cs, c["W"], width=4, **rule)
+    assert s["converged"].all()
+    assert max(s["rel_pri"].max(), s["rel_dual"].max()) <= TOL
+    gap = np.abs(s["obj"] - c["opt"]) / np.maximum(1.0, np.abs(c["opt"]))
+    assert gap.max() <= 1e-3
+    it_b = lgk.fetch_stats(lgk.solve_weightings(cs, c["W"], None, **rule))["iters"]
+    assert np.all(np.abs(s["iters"] - it_b) <= 0.2 * it_b + 100), (s["iters"], it_b)
+    t = s["t"]
+    assert np.all(t >= 0) and np.all(s["tau"] >= 0)
+    met = M.plan_metrics(M.dose(c["phi_eval"], t.T), c["label"], c["case"].d_presc, t.T,
+                         c["case"].n_iso)
+    for key in ("coverage", "selectivity", "gi", "bot"):
+        rel = np.abs(met[key] - c["met_ref"][key]) / np.abs(c["met_ref"][key])
+        assert rel.max() <= 5e-3, (key, rel)
+
+
+def test_stream_width_one_and_iteration_cap(lgk, cfg0):
+    """Width 1 (every weighting alone, 8 refills) and a per-weighting cap of
+    60 iterations: every weighting stops unconverged after its own 60-109
+    iterations (the cap is applied at graph boundaries, every 50), and the
+    stream ends."""
+    c = cfg0
+    cs = make(lgk, c["case"], 2)
+    s = lgk.solve_stream(cs, c["W"], w0_bot=SC.W0_BOT, rho0=L.rho0_for(c["lp"]), tol=TOL,
+                         max_iter=60, width=1)
+    assert not s["converged"].any()
+    assert np.all((s["iters"] >= 60) & (s["iters"] < 110)), s["iters"]
+    assert np.isfinite(s["t"]).all() and (s["t"] >= 0).all()
