@@ -270,14 +270,14 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel source
-    is unchanged since it was taken."""
+def committed_traffic(kernel, workload, k_launch):
+    """DRAM bytes per launch from a committed ncu summary of the same workload
+    and launch width, if the kernel source is unchanged since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-        e = t[workload][kernel]
+        e = t[f"{workload}_k{k_launch}"][kernel]
         return e["bytes_per_launch"] if e.get("source_hash") == kernel_hash() else None
     except (OSError, KeyError, ValueError):
         return None
@@ -448,7 +448,7 @@ def run_ours(args, rank, world, local):
         roof["executed_tensor_frac"] = executed / (ms_avg / 1e3) / (tf_sus * 1e12)
         roof["executed_bytes_per_launch"] = xbytes
         roof["executed_hbm_frac"] = xbytes / (ms_avg / 1e3) / (hbm * 1e9)
-        roof["traffic"] = committed_traffic(dom, args.workload)
+        roof["traffic"] = committed_traffic(dom, args.workload, k_launch)
         roof["kernel"] = dom
         roof["peak_source"] = (f"{src} (MEASURED_PEAKS.json; hbm_gbs, bf16_tflops_sustained)"
                                if src == "measured" else "fallback")
