@@ -289,7 +289,7 @@ int lgk_solve_weightings_masked(lgk_case* cs, int K, const double* W, const doub
  *   prof_ms, prof_launches (LGK_K_COUNT): per-kernel CUDA-event time and
  *        launches as lgk_fetch_profile (only with lgk_params.profile = 1).
  * 1 <= K_total <= 1 << 20.  LGK_EINVAL on bad arguments; on any error the
- * outputs are undefined.
+ * outputs are undefined.  lgk_params.timeout_ms bounds the whole stream.
  */
 int lgk_solve_stream(lgk_case* cs, int K_total, const double* W, const double* rho, double w0_bot,
                      double rho0, double tol, int max_iter, int width, double* t, double* tau, int* iters,
