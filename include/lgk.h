@@ -106,9 +106,10 @@ typedef struct {
                                 read half the bytes.
                                 0: both terms every iteration (the literal iteration).      */
     int lo_refresh_iters;    /* with lo_refresh = 1: once a solve has run this many iterations
-                                with columns still active, it continues with the literal
-                                iteration (a safety net for columns the lagged products slow
-                                down); 0 = never.  Default 8000.                             */
+                                with columns still active (a stream: once its oldest running
+                                column has), it continues with the literal iteration (a
+                                safety net for columns the lagged products slow down);
+                                0 = never.  Default 8000.                                   */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
