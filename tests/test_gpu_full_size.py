@@ -1,0 +1,76 @@
+"""GPU checks at full size, in the launch configuration the benchmark times:
+the 3750 x 41200 case (ellipsoid, 150 isocenters, 40000 points), its 81
+slider weightings streamed through 32 columns, slowest (lowest w_BOT) first,
+BF16X3 form with the lagged low term, tol 1e-4.
+
+The oracle cannot solve these LPs in a test's time, so the checks are
+properties that hold at any size plus per-plan quantities the oracle
+evaluates one plan at a time in FP64:
+  * every weighting converges (relative residuals <= 1e-4 as reported);
+  * strong duality at the approximate optimum: for sampled plans, the
+    weighted-sum objective of Sec. 2.A evaluated by the oracle at the
+    device's multipliers (sector and isocenter times) equals minus the
+    device's dual objective c^T z to 2e-3 (each side within the 1e-3
+    objective bar; the FP64 oracle ADMM itself reaches <= 6.6e-4 on the
+    9-weighting sphere case at this tolerance);
+  * the hard constraints (BOT coupling tau >= C_S t per isocenter, u = inf
+    columns: (c + A^T lam)_j >= 0) hold to 4 tol ||A||_2 max|lam|: a stop at
+    relative residual tol leaves the multipliers off by about tol relative,
+    and A^T scales that by at most ||A||_2 (32.2 here, 12.0 on the sphere
+    case, where the FP64 oracle ADMM's violation is 1.7e-4 max|lam| against
+    tol ||A||_2 = 1.2e-3).
+"""
+import numpy as np
+import pytest
+
+from oracle import kkt as KK
+from oracle import lp as L
+from synth import cases as SC
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def lgk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_08602_b300 import build
+    build.build()
+    from paper_2509_08602_b300 import lgk as mod
+    return mod
+
+
+def test_streamed_81_weightings_full_size(lgk):
+    case = SC.workload_case(1)
+    W = SC.slider_weights(SC.WORKLOADS[1]["grid"])
+    W = W[np.argsort(W[:, 3], kind="stable")]
+    lp = L.precondition(L.assemble_case(case))
+    cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                         case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal)
+    assert (cs.m, cs.n) == (lp.m, lp.n) == (3750, 41200)
+    s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=L.rho0_for(lp), tol=TOL, max_iter=20000,
+                         width=32)
+    assert s["converged"].all()
+    assert max(s["rel_pri"].max(), s["rel_dual"].max()) <= TOL
+    assert np.isfinite(s["t"]).all() and (s["t"] >= 0).all() and (s["tau"] >= 0).all()
+    # ||A||_2 by power iteration on A A^T
+    v = np.random.default_rng(0).standard_normal(lp.m)
+    for _ in range(60):
+        v = lp.A @ (lp.A.T @ v)
+        nrm = np.linalg.norm(v)
+        v /= nrm
+    a_norm = np.sqrt(nrm)
+    rng = np.random.default_rng(81)
+    sample = np.unique(np.concatenate([[0, 1, 80], rng.choice(81, size=3, replace=False)]))
+    b, _, u = L.bounds(lp, W[sample])
+    rows = []
+    for c, w in enumerate(sample):
+        lam = np.concatenate([s["t"][w], s["tau"][w]]) / lp.row_scale      # scaled multipliers
+        obj, viol = KK.planning_objective(lp.A, b[:, c], lp.c, u[:, c], lam)
+        dual = s["obj"][w]
+        rows.append((int(w), abs(dual + obj) / max(1.0, abs(dual)), viol / np.abs(lam).max()))
+    assert all(g <= 2e-3 for _, g, _ in rows), rows
+    assert all(r <= 4 * TOL * a_norm for _, _, r in rows), (a_norm, rows)
