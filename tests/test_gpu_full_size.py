@@ -74,3 +74,4 @@ def test_streamed_81_weightings_full_size(lgk):
         rows.append((int(w), abs(dual + obj) / max(1.0, abs(dual)), viol / np.abs(lam).max()))
     assert all(g <= 2e-3 for _, g, _ in rows), rows
     assert all(r <= 4 * TOL * a_norm for _, _, r in rows), (a_norm, rows)
+    cs.close()
