@@ -286,7 +286,9 @@ int lgk_solve_weightings_masked(lgk_case* cs, int K, const double* W, const doub
  *   width: columns iterated at once, 1 <= width <= 4096.
  * Outputs (host arrays, each may be NULL), per weighting in input order:
  *   t (K_total x 24N), tau (K_total x N): as lgk_fetch_times;
- *   iters, obj, rel_pri, rel_dual, converged (K_total): as lgk_fetch_stats;
+ *   iters, obj, rel_pri, rel_dual, converged (K_total): as lgk_fetch_stats
+ *        (the residuals of the weighting's last residual test; 0 with tol = 0,
+ *        which runs none);
  *   prof_ms, prof_launches (LGK_K_COUNT): per-kernel CUDA-event time and
  *        launches as lgk_fetch_profile (only with lgk_params.profile = 1).
  * 1 <= K_total <= 1 << 20.  LGK_EINVAL on bad arguments; on any error the
