@@ -457,8 +457,8 @@ def run_ours(args, rank, world, local):
         roof["avg_launch_ms"] = ms_avg
         total_ms = sum(v[0] for v in prof.values())
         roof["kernel_share"] = {k: round(v[0] / total_ms, 4) for k, v in prof.items()}
-        roof["timing"] = (f"CUDA events around every kernel of one profiled solve of the same batch "
-                          f"({prof_iters} iterations); the timed steps run without them")
+        roof["timing"] = (f"CUDA events around every kernel of one profiled solve of the same workload "
+                          f"and batching ({prof_iters} iterations); the timed steps run without them")
         # iterations per step: the batch runs until its slowest column stops;
         # a stream's count is that of its profiled run (the same schedule)
         roof["us_per_iteration_timed"] = t_max / args.steps / (prof_iters if sw else max_iters) * 1e6
