@@ -174,6 +174,15 @@ def allreduce_sum(x, world):
     return float(t.item())
 
 
+def passes(st, ck, tol):
+    """Plans counted as converged: the device's residual test passed (relative
+    residuals <= tol) and the FP64 check of the plan against its exact LP
+    holds: duality gap <= 1e-3 relative and backward-error infeasibility of
+    A z1 <= b at most tol (lgk_fetch_check)."""
+    return (np.asarray(st["converged"], dtype=bool) & (np.abs(ck["gap"]) <= 1e-3)
+            & (ck["infeas"] <= tol))
+
+
 def make_inputs(cfg):
     from synth import cases as SC
     case = SC.workload_case(cfg)
@@ -181,7 +190,30 @@ def make_inputs(cfg):
     return case, W
 
 
-def oracle_sample(case, W, iters_to_converge, budget_s=30.0):
+def oracle_iters(workload):
+    """Mean iterations per plan of the FP64 oracle ADMM at tol 1e-4 on this
+    workload, as recorded by tests/golden/make_oracle_iters.py (oracle only),
+    or None if not recorded."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_iters.json")) as f:
+            e = json.load(f)[workload]
+        return float(e["mean_iters"]), e["sample"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def iteration_basis(workload):
+    """Iterations per plan by which both CPU figures extrapolate one timed
+    oracle iteration: the oracle's own recorded mean, else the paper's fixed
+    count (Sec. 3.D)."""
+    rec = oracle_iters(workload)
+    if rec:
+        return rec[0], (f"the FP64 oracle's own mean of {rec[0]:.0f} iterations per plan at "
+                        f"tol 1e-4 ({rec[1]}; tests/golden/oracle_iters.json)")
+    return float(PAPER_ITERS), f"the paper's fixed {PAPER_ITERS} iterations (Sec. 3.D)"
+
+
+def oracle_sample(case, W, iters_to_converge, basis, budget_s=30.0):
     """Time the FP64 oracle ADMM (as it stands) on the host cores: a bounded
     number of iterations over all K columns; per-iteration time is the
     difference to a zero-iteration run (which still forms and factors S)."""
@@ -206,7 +238,7 @@ def oracle_sample(case, W, iters_to_converge, budget_s=30.0):
                 sample=(f"FP64 oracle ADMM (numpy/LAPACK) on {case.name}, all {K} weightings, "
                         f"{n_it} iterations timed after S formation+Cholesky ({t_setup:.1f} s, "
                         f"excluded like the device's case set-up); {t_iter * 1e3:.1f} ms/iteration "
-                        f"extrapolated to {iters_to_converge:.0f} iterations per plan"))
+                        f"extrapolated to {basis}"))
 
 
 def run_reference(args, rank, world):
@@ -232,7 +264,8 @@ def run_reference(args, rank, world):
         if s >= args.warmup:
             times.append(max(dt, 1e-9))
     t_iter = statistics.median(times)
-    value = K / (t_iter * PAPER_ITERS)
+    n_iters, basis = iteration_basis(args.workload)
+    value = K / (t_iter * n_iters)
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "plans/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -242,8 +275,7 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "plans/s", "cores": cores, "kind": "oracle",
                              "sample": (f"one FP64 oracle ADMM iteration over all {K} weightings "
                                         f"per step (S formation+Cholesky, {t_setup:.1f} s, "
-                                        f"subtracted), extrapolated to the paper's fixed "
-                                        f"{PAPER_ITERS} iterations (Sec. 3.D)")},
+                                        f"subtracted), extrapolated to {basis}")},
             "e2e": {"value": value, "unit": "plans/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -329,20 +361,24 @@ def run_ours(args, rank, world, local):
     ev0.record()
     t_host0 = time.perf_counter()
     r_last = None
+    checks = []
     for _ in range(args.steps):
         t1 = time.perf_counter()
         if sw:
-            st = lgk.solve_stream(cs, W, None, width=sw, **rule)
+            st = lgk.solve_stream(cs, W, None, width=sw, check=True, **rule)
+            ck = st["check"]
             lat.append(time.perf_counter() - t1)
         else:
             r = lgk.solve_weightings(cs, W, None, **rule)
-            lat.append(time.perf_counter() - t1)
             st = lgk.fetch_stats(r)
+            ck = lgk.fetch_check(r)
+            lat.append(time.perf_counter() - t1)
             if r_last is not None:
                 r_last.close()
             r_last = r
-        conv += int(st["converged"].sum())
+        conv += int(passes(st, ck, args.tol).sum())
         iters.append(st["iters"])
+        checks.append(ck)
     ev1.record()
     torch.cuda.synchronize()
     barrier(world)
@@ -390,13 +426,13 @@ def run_ours(args, rank, world, local):
                                                        lo_refresh=int(refine),
                                                        check_every=args.check_every))
         if sw:
-            s2 = lgk.solve_stream(c2, W, None, width=sw, **rule)
+            s2 = lgk.solve_stream(c2, W, None, width=sw, check=True, **rule)
             t, tau = s2["t"], s2["tau"]
-            conv_e2e += int(s2["converged"].sum())
+            conv_e2e += int(passes(s2, s2["check"], args.tol).sum())
         else:
             r = lgk.solve_weightings(c2, W, None, **rule)
             t, tau = lgk.fetch_times(r)
-            conv_e2e += int(lgk.fetch_stats(r)["converged"].sum())
+            conv_e2e += int(passes(lgk.fetch_stats(r), lgk.fetch_check(r), args.tol).sum())
             r.close()
         c2.close()
     torch.cuda.synchronize()
@@ -413,21 +449,9 @@ def run_ours(args, rank, world, local):
             c3 = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                                  case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                                  params=lgk.default_params(precision=lgk.PREC_FP32, device=local))
-            r = lgk.solve_weightings(c3, W, None, **rule)
-            r.close()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = lgk.solve_weightings(c3, W, None, **rule)
-            dt = time.perf_counter() - t0
-            s3 = lgk.fetch_stats(r)
-            n3 = int(s3["converged"].sum())
-            fp32 = {"value": n3 / dt, "unit": "plans/s", "mean_iters": float(s3["iters"].mean()),
-                    "converged": n3, "K": K, "max_iter": args.max_iter,
-                    "all_converged": bool(s3["converged"].all()),
-                    "ratio_over_fp32": (value / world) / (n3 / dt) if n3 else None,
-                    "median_rel_pri": float(np.median(s3["rel_pri"])),
-                    "median_rel_dual": float(np.median(s3["rel_dual"]))}
-            r.close()
+            fp32 = fp32_form(lgk, c3, W, rule, sw, args.tol)
+            fp32["ratio_over_fp32"] = (value / world) / fp32["value"] if fp32["value"] else None
+            fp32["max_iter"] = args.max_iter
             c3.close()
         hbm, tf_burst, tf_sus, src = peaks()
         m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
@@ -465,12 +489,15 @@ def run_ours(args, rank, world, local):
         roof["us_per_iteration_profiled"] = total_ms / prof_iters * 1e3
         cpu = None
         if not args.no_cpu_baseline:
-            cpu = oracle_sample(case, W, mean_iters)
+            n_iters, basis = iteration_basis(args.workload)
+            cpu = oracle_sample(case, W, n_iters, basis)
         if not args.no_extras and r_last is None:     # streaming: one batch solve for the extras
             r_last = lgk.solve_weightings(cs, W, None, **rule)
         extra = {} if args.no_extras else {
             "plan_metrics": bench_metrics(lgk, case, r_last),
             "two_pass": bench_two_pass(lgk, case, W, args, local)}
+        if not args.no_k441 and args.workload == "cfg1":
+            extra["k441"] = bench_k441(lgk, args, local)
         lat_ms = sorted(x * 1e3 for x in lat)
         out = {"metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -489,12 +516,122 @@ def run_ours(args, rank, world, local):
                               "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]},
                "mean_iters_per_plan": mean_iters, "max_iters": max_iters,
                "converged_fraction": conv / (K * args.steps),
+               "fp64_check": check_summary(checks),
                "fp32_form": fp32, **extra}
         print(json.dumps(out), flush=True)
     if r_last is not None:
         r_last.close()
     cs.close()
     return 0
+
+
+def bench_k441(lgk, args, local, width=128, steps=2, fp32_max_iter=4000):
+    """The 441-weighting half of the metric: the 4-target 5000 x 61600 case,
+    its 21 x 21 slider grid streamed through `width` columns (lowest w_BOT
+    first), one untimed and `steps` timed streams on the device (case
+    resident), plans counted with the FP64 check; e2e = create_case from
+    pinned host phi + stream + times; and the plain FP32 form through the same
+    width, bounded at fp32_max_iter iterations per weighting (it stalls above
+    tol at this size)."""
+    import torch
+    from synth import cases as SC
+    case, W = make_inputs(2)
+    W = W[np.argsort(W[:, 3], kind="stable")]
+    K = W.shape[0]
+    prec = PRECISIONS[args.precision]
+    refine = args.precision == "bf16x3" and not args.exact
+    params = lgk.default_params(precision=prec, device=local, lo_refresh=int(refine),
+                                check_every=args.check_every)
+    cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                         case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, params=params)
+    rule = dict(w0_bot=SC.W0_BOT, rho0=RHO0_PER_BETA * cs.beta, tol=args.tol, max_iter=args.max_iter)
+    lgk.solve_stream(cs, W, None, width=width, **rule)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv, its, cks = 0, [], []
+    for _ in range(steps):
+        st = lgk.solve_stream(cs, W, None, width=width, check=True, **rule)
+        conv += int(passes(st, st["check"], args.tol).sum())
+        its.append(st["iters"])
+        cks.append(st["check"])
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    cs.close()
+    phi_pinned = torch.empty(case.phi.shape, dtype=torch.float64, pin_memory=True).numpy()
+    phi_pinned[...] = case.phi
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c2 = lgk.create_case(phi_pinned, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                         case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, params=params)
+    s2 = lgk.solve_stream(c2, W, None, width=width, check=True, **rule)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    conv_e2e = int(passes(s2, s2["check"], args.tol).sum())
+    c2.close()
+    fp32 = None
+    if not args.no_fp32:
+        c3 = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
+                             case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                             params=lgk.default_params(precision=lgk.PREC_FP32, device=local))
+        rule32 = dict(rule, max_iter=fp32_max_iter)
+        t0 = time.perf_counter()
+        s3 = lgk.solve_stream(c3, W, None, width=width, check=True, **rule32)
+        d3 = time.perf_counter() - t0
+        n3 = int(passes(s3, s3["check"], args.tol).sum())
+        fp32 = {"value": n3 / d3, "unit": "plans/s", "converged": n3, "K": K,
+                "max_iter": fp32_max_iter, "seconds": d3,
+                "median_rel_pri": float(np.median(s3["rel_pri"])),
+                "median_rel_dual": float(np.median(s3["rel_dual"])),
+                "ratio_over_fp32": (conv / steps / dt) / (n3 / d3) if n3 else None}
+        c3.close()
+    it = np.concatenate(its)
+    m, n = 25 * case.n_iso, case.n_pts + 8 * case.n_iso
+    return {"workload": f"{case.name} (A {m}x{n}, K={K} weightings, tol {args.tol:g})",
+            "value": conv / steps / dt, "unit": "plans/s", "converged": conv / steps, "K": K,
+            "s_per_step": dt, "steps": steps, "batching": f"stream through {width} columns",
+            "mean_iters_per_plan": float(it.mean()), "max_iters": int(it.max()),
+            "fp64_check": check_summary(cks),
+            "e2e": {"value": conv_e2e / e2e_s, "unit": "plans/s", "seconds": e2e_s,
+                    "h2d_bytes_per_step": int(case.phi.nbytes + case.kind.nbytes
+                                              + case.struct_id.nbytes + W.nbytes),
+                    "d2h_bytes_per_step": int(s2["t"].nbytes + s2["tau"].nbytes)},
+            "fp32_form": fp32}
+
+
+def check_summary(checks):
+    """Worst values of the FP64 plan check over the timed steps."""
+    ck = {k: np.concatenate([c[k] for c in checks]) for k in checks[0]}
+    return {"max_abs_gap": float(np.max(np.abs(ck["gap"]))), "max_infeas": float(np.max(ck["infeas"])),
+            "max_hard": float(np.max(ck["hard"])), "max_bound": float(np.max(ck["bound"])),
+            "note": "lgk_fetch_check per plan (FP64 A z1, A^T lam against the exact LP); a plan "
+                    "counts as converged when its residual test passed, |gap| <= 1e-3 and "
+                    "infeas <= tol"}
+
+
+def fp32_form(lgk, c3, W, rule, sw, tol):
+    """The plain FP32 GPU form (cuBLAS SGEMM, FP32 S^-1) on the same weightings
+    and batching as the measured form (streamed through the same width, or one
+    batch), so the ratio compares precision forms alone; one untimed run,
+    then one timed.  Plans are counted as in the measured form."""
+    def once():
+        if sw:
+            s3 = lgk.solve_stream(c3, W, None, width=sw, check=True, **rule)
+            return s3, s3["check"]
+        r = lgk.solve_weightings(c3, W, None, **rule)
+        out = lgk.fetch_stats(r), lgk.fetch_check(r)
+        r.close()
+        return out
+    once()
+    t0 = time.perf_counter()
+    s3, ck = once()
+    dt = time.perf_counter() - t0
+    n3 = int(passes(s3, ck, tol).sum())
+    K = W.shape[0]
+    return {"value": n3 / dt, "unit": "plans/s", "mean_iters": float(np.mean(s3["iters"])),
+            "converged": n3, "K": K, "all_converged": n3 == K,
+            "batching": f"stream through {sw} columns" if sw else f"one batch of {K}",
+            "median_rel_pri": float(np.median(s3["rel_pri"])),
+            "median_rel_dual": float(np.median(s3["rel_dual"]))}
 
 
 def bench_metrics(lgk, case, res, reps=3):
@@ -692,6 +829,8 @@ def main():
                     help="BF16 form of A: bf16x3 (two BF16 terms; the plans match FP64), bf16 (one term)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the device plan-metrics and two-pass measurements")
+    ap.add_argument("--no-k441", action="store_true",
+                    help="skip the 441-weighting (5000 x 61600) measurement of the cfg1 line")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of requests of a Poisson stream")
     ap.add_argument("--serve-workers", type=int, default=2)

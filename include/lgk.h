@@ -110,6 +110,18 @@ typedef struct {
                                 column has), it continues with the literal iteration (a
                                 safety net for columns the lagged products slow down);
                                 0 = never.  Default 8000.                                   */
+    int rho_adapt;           /* 1: adapt each column's rho during the solve by residual
+                                balancing (Boyd et al., Sec. 3.4.1 of their ADMM monograph):
+                                at every graph replay boundary (5 x check_every iterations),
+                                with the relative residuals of that iteration's test, rho is
+                                multiplied by 1.5 when rel_pri > 3 rel_dual and divided by
+                                1.5 when rel_dual > 3 rel_pri, at most 40 times per column
+                                (then fixed, so the iteration converges as with a fixed rho).
+                                S = A A^T + I does not depend on rho (Sec. 2.B), so a change
+                                only rescales the column's scaled duals y by rho_old/rho_new
+                                (the multipliers rho y are unchanged).  The stop test and
+                                the reported plans use the column's current rho.
+                                0 (default): rho fixed per column (Eq. rho_rule or caller's). */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
@@ -161,6 +173,30 @@ int lgk_solve_weightings(lgk_case* cs, int K, const double* W, const double* rho
                          double w0_bot, double rho0, double tol, int max_iter,
                          lgk_result** out);
 
+/*
+ * lgk_solve_weightings_async -- lgk_solve_weightings without blocking.
+ *
+ * Same arguments, checks and iteration (Sec. 2.B) as lgk_solve_weightings;
+ * the solve runs on a library thread and *out is returned at once.  Until
+ * lgk_wait(*out, ...) has returned LGK_OK, every fetch on *out returns
+ * LGK_EINVAL, and the case is busy: another solve of it returns LGK_EINVAL.
+ * W and rho are copied before the call returns.  Freeing the result while
+ * the solve runs stops the solve at its next graph replay (within 5 residual-
+ * test intervals) and waits for that.
+ */
+int lgk_solve_weightings_async(lgk_case* cs, int K, const double* W, const double* rho,
+                               double w0_bot, double rho0, double tol, int max_iter,
+                               lgk_result** out);
+
+/*
+ * lgk_wait -- wait at most timeout_ms (>= 0; 0 polls) for the asynchronous
+ * solve of res.  LGK_OK once it finished successfully (the result may then be
+ * fetched); LGK_ETIMEOUT if it is still running (call again later); the
+ * solve's own error code if it failed.  A result from any other solve call
+ * returns LGK_OK at once.
+ */
+int lgk_wait(lgk_result* res, int timeout_ms);
+
 /* Sector times t (K x 24N, minutes) and isocenter beam-on times tau (K x N,
  * normalised units of the LP) of each plan: the multipliers rho * y2 of
  * A x <= b, unscaled by the row scale (Sec. 2.B: the primal solution is rho y*).
@@ -198,9 +234,15 @@ int lgk_fetch_doses(const lgk_result* res, const double* phi_eval, int n_eval, d
  * calls share the one array, so calls that overlap on the GPU (from several
  * host threads, or on several streams) race with each other and must be
  * serialised by the caller.
- * The first call on a device looks up the scratch array's device address
- * (once per device); make that first call before any stream capture.
- * Runs on the case's stream and returns when the doses are written.
+ * The first call on a device looks up the scratch array's device address;
+ * make that first call before any stream capture.  Every later call made
+ * outside a stream capture looks the address up again, so an address found
+ * before a device reset is not reused after it.
+ * Ordering: the call runs on the case's stream (lgk_params.stream, or the
+ * library's own), not on the caller's.  The caller must finish writing
+ * phi_eval_dev before the call (e.g. synchronise the stream that wrote it);
+ * the call synchronises the case's stream before it returns, so dose_dev is
+ * complete on return.  The caller's current device is unchanged on return.
  * Errors: LGK_EINVAL, LGK_ECUDA.
  */
 #define LGK_NOALLOC_MAX_TIMES (1 << 22)
@@ -230,6 +272,40 @@ int lgk_fetch_metrics(const lgk_result* res, const double* phi_eval, int n_eval,
  * and dual residuals at the last test, converged flag. */
 int lgk_fetch_stats(const lgk_result* res, int* iters, double* obj, double* rel_pri,
                     double* rel_dual, uint8_t* converged);
+
+/*
+ * lgk_fetch_check -- FP64 check of each plan against its exact LP.
+ *
+ * Sec. 2.B recovers the plan (sector and isocenter times) from the scaled
+ * multipliers rho y2 of the final iterate; the iterations themselves run in
+ * BF16/FP32 and stop on FP32 residual sums.  This call re-evaluates every
+ * column on the device in FP64, from z1 = clip(q1, 0, u) and
+ * lam = rho max(q2 - b, 0) as the library holds them, against the LP of
+ * Eq. dual_problem with its bounds u and b computed in FP64 (Appendix A), and
+ * with A the matrix the iterations use (its BF16 terms summed exactly, or its
+ * FP32 copy).  A z1 and A^T lam are FP64 dot products.
+ * out: K x LGK_CHECK_COUNT host array, per column:
+ *   LGK_CHECK_OBJ        c^T z1 (the dual LP's objective)
+ *   LGK_CHECK_PLAN       b^T lam + sum over finite-u columns of u (-(c + A^T lam))_+:
+ *                        the weighted-sum objective of Sec. 2.A at the plan
+ *   LGK_CHECK_GAP        (c^T z1 + plan) / max(1, |c^T z1|): relative duality gap
+ *                        (the optimum lies between -plan and c^T z1 when both
+ *                        points are feasible)
+ *   LGK_CHECK_INFEAS     ||(A z1 - b)_+||_2 / || |A| z1 ||_2: normwise backward
+ *                        error of A z1 <= b (constraint rows cancel large
+ *                        terms; this measures the violation against them)
+ *   LGK_CHECK_INFEAS_ABS ||(A z1 - b)_+||_2
+ *   LGK_CHECK_HARD       max over u = inf columns (organ limits, BOT coupling)
+ *                        of (-(c + A^T lam))_+, divided by max lam
+ *   LGK_CHECK_BOUND      max over finite-u columns of (z1 - u)_+ (the iterations
+ *                        clip to FP32 copies of u)
+ * Runs on the case's stream; device temporaries of about
+ * 64 x (2 n + 2.5 m) doubles are allocated on first use and kept with the
+ * result.  Errors: LGK_EINVAL, LGK_ENOMEM, LGK_ECUDA.
+ */
+enum { LGK_CHECK_OBJ = 0, LGK_CHECK_PLAN = 1, LGK_CHECK_GAP = 2, LGK_CHECK_INFEAS = 3,
+       LGK_CHECK_INFEAS_ABS = 4, LGK_CHECK_HARD = 5, LGK_CHECK_BOUND = 6, LGK_CHECK_COUNT = 7 };
+int lgk_fetch_check(const lgk_result* res, double* out);
 
 /*
  * lgk_solve_weightings_warm -- as lgk_solve_weightings, but starting from a
@@ -290,14 +366,19 @@ int lgk_solve_weightings_masked(lgk_case* cs, int K, const double* W, const doub
  *        (the residuals of the weighting's last residual test; 0 with tol = 0,
  *        which runs none);
  *   prof_ms, prof_launches (LGK_K_COUNT): per-kernel CUDA-event time and
- *        launches as lgk_fetch_profile (only with lgk_params.profile = 1).
- * 1 <= K_total <= 1 << 20.  LGK_EINVAL on bad arguments; on any error the
+ *        launches as lgk_fetch_profile (only with lgk_params.profile = 1);
+ *   check (K_total x LGK_CHECK_COUNT): the FP64 check of lgk_fetch_check,
+ *        run on each weighting's column when it stops (before the column is
+ *        refilled).
+ * 1 <= K_total <= 1 << 20, and (ceil(K_total / width) + 1) x (max_iter
+ * rounded up to a graph replay, plus one replay) <= 2^30 (the stream's
+ * iteration counter is 32-bit).  LGK_EINVAL on bad arguments; on any error the
  * outputs are undefined.  lgk_params.timeout_ms bounds the whole stream.
  */
 int lgk_solve_stream(lgk_case* cs, int K_total, const double* W, const double* rho, double w0_bot,
                      double rho0, double tol, int max_iter, int width, double* t, double* tau, int* iters,
                      double* obj, double* rel_pri, double* rel_dual, uint8_t* converged, double* prof_ms,
-                     long long* prof_launches);
+                     long long* prof_launches, double* check);
 
 /* ------------------------------------------------------------------------
  * Two-pass optimisation (Sec. 2.C).  The first pass takes its low-dose

@@ -28,16 +28,15 @@ r = x' - z' and s = rho (z' - z), column j stops once
     ||s|| <= eps_abs sqrt(n+m) + tol ||rho y'||,
 checked every `check_every` iterations; a stopped column keeps its iterate.
 
-Lagged low term (`lagged_lo`, the device's default iteration for the
-two-term BF16 form; not in the paper): with A = A_hi + E, the two products
-of an iteration use A_hi and add E applied to the operands of the last
-"full" iteration, r1_f and v_f:
-    A r1   ~  A_hi r1 + E r1_f,        A^T v  ~  A_hi^T v + E^T v_f.
-Full iterations use A itself and refresh r1_f, v_f: the first one and every
-`refresh`-th (the residual-test iterations, k + 1 = 0 mod refresh); `restart`
-(0 for none) adds the iterations k = 0 mod restart.  A fixed point of this
-iteration has r1 = r1_f, v = v_f, hence is a fixed point of the literal
-iteration with A.
+Per-column penalty adaptation (`balance`, optional; not in the paper, which
+fixes rho per weighting by Eq. rho_rule): residual balancing (Boyd et al.,
+Sec. 3.4.1 of their monograph) applied per column every `every` iterations
+(a multiple of check_every, so the residuals of that iteration's test are
+used): if rel_pri > mu rel_dual then rho <- tau rho, if rel_dual > mu rel_pri
+then rho <- rho / tau, at most `max_changes` times per column.  S = A A^T + I
+does not depend on rho (Sec. 2.B), so a change costs only the rescaling of
+the scaled dual variables, y <- y rho_old / rho_new, which keeps the
+unscaled multipliers rho y.
 """
 from __future__ import annotations
 
@@ -73,14 +72,14 @@ class AdmmResult:
 
 def admm(A, c, b, l, u, rho, *, max_iter: int, tol: float | None = None,
          check_every: int = 10, eps_abs: float = 1e-12, state=None,
-         lagged_lo=None) -> AdmmResult:
+         balance=None) -> AdmmResult:
     """Run the literal ADMM iteration above for all K columns.
 
     A (m, n); c (n,); b (m, K); l, u (n, K); rho (K,).  With tol=None every
     column runs exactly `max_iter` iterations.  `state` optionally gives
     (z1, z2, y1, y2) to start from (default zeros, as the paper is silent).
-    `lagged_lo` = (A_hi, refresh, restart) runs the lagged-low-term variant
-    described in the module docstring (S is formed from A in both cases).
+    `balance` = (every, mu, tau, max_changes) turns on the per-column penalty
+    adaptation described in the module docstring (needs tol).
     """
     A = np.asarray(A, dtype=np.float64)
     m, n = A.shape
@@ -101,30 +100,15 @@ def admm(A, c, b, l, u, rho, *, max_iter: int, tol: float | None = None,
     rel_pri = np.full(K, np.inf)
     rel_dual = np.full(K, np.inf)
     sq = np.sqrt(n + m)
-    if lagged_lo is not None:
-        A_hi, refresh, restart = lagged_lo
-        A_hi = np.asarray(A_hi, dtype=np.float64)
-        E = A - A_hi
-        r1_f, v_f = np.zeros((n, K)), np.zeros((m, K))
+    changes = np.zeros(K, dtype=np.int64)
+    c = np.asarray(c, dtype=np.float64)
     for k in range(max_iter):
         if not active.any():
             break
         a = np.flatnonzero(active)
         r1 = z1[:, a] - y1[:, a] - c_over_rho[:, a]
-        full = (lagged_lo is None or k == 0 or (k + 1) % refresh == 0
-                or (restart > 0 and k % restart == 0))
-        if full:
-            Ar1 = A @ r1
-        else:
-            Ar1 = A_hi @ r1 + E @ r1_f[:, a]
-        v = scipy.linalg.cho_solve(cf, Ar1 - z2[:, a] + y2[:, a])
-        if full:
-            ATv = A.T @ v
-            if lagged_lo is not None:
-                r1_f[:, a], v_f[:, a] = r1, v
-        else:
-            ATv = A_hi.T @ v + E.T @ v_f[:, a]
-        nx1 = r1 - ATv
+        v = scipy.linalg.cho_solve(cf, A @ r1 - z2[:, a] + y2[:, a])
+        nx1 = r1 - A.T @ v
         nx2 = v + z2[:, a] - y2[:, a]
         nz1 = np.clip(nx1 + y1[:, a], l[:, a], u[:, a])
         nz2 = np.minimum(nx2 + y2[:, a], b[:, a])
@@ -147,6 +131,22 @@ def admm(A, c, b, l, u, rho, *, max_iter: int, tol: float | None = None,
             done = (rn <= eps_abs * sq + tol * np.maximum(xn, zn)) & \
                    (sn <= eps_abs * sq + tol * yn)
             active[a[done]] = False
+            if balance is not None and (k + 1) % balance[0] == 0:
+                _, mu, tau, max_changes = balance
+                for i, j in enumerate(a):
+                    if done[i] or changes[j] >= max_changes:
+                        continue
+                    if rel_pri[j] > mu * rel_dual[j]:
+                        f = tau
+                    elif rel_dual[j] > mu * rel_pri[j]:
+                        f = 1.0 / tau
+                    else:
+                        continue
+                    y1[:, j] /= f
+                    y2[:, j] /= f
+                    rho[j] *= f
+                    c_over_rho[:, j] = c / rho[j]
+                    changes[j] += 1
     converged = ~active if tol is not None else np.zeros(K, dtype=bool)
     return AdmmResult(z1=z1, z2=z2, y1=y1, y2=y2, x1=x1, x2=x2, iters=iters,
                       converged=converged, rel_pri=rel_pri, rel_dual=rel_dual, rho=rho)

@@ -2,9 +2,11 @@
 #include <math.h>
 
 #include <algorithm>
+#include <chrono>
 #include <memory>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "lgk_impl.hpp"
 
@@ -46,6 +48,15 @@ static bool finite_pos(const double* a, size_t n) {
     return true;
 }
 
+// A result's solve has finished and, if it ran asynchronously, lgk_wait has
+// reported its success: its results may be read.
+int result_ready(ResultData& d) {
+    std::lock_guard<std::mutex> lk(d.amu);
+    if (!d.waited) return fail(LGK_EINVAL, "asynchronous solve not waited for: call lgk_wait first");
+    if (d.async_rc) return fail(LGK_EINVAL, "the asynchronous solve of this result failed");
+    return LGK_OK;
+}
+
 }  // namespace lgk
 
 using namespace lgk;
@@ -66,6 +77,7 @@ int lgk_default_params(lgk_params* p) {
     p->profile = 0;
     p->lo_refresh = 1;
     p->lo_refresh_iters = 8000;
+    p->rho_adapt = 0;
     return LGK_OK;
 }
 
@@ -78,6 +90,7 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     if (p) prm = *p;
     if (prm.lo_refresh != 0 && prm.lo_refresh != 1) return fail(LGK_EINVAL, "lo_refresh must be 0 or 1");
     if (prm.lo_refresh_iters < 0) return fail(LGK_EINVAL, "lo_refresh_iters must be >= 0");
+    if (prm.rho_adapt != 0 && prm.rho_adapt != 1) return fail(LGK_EINVAL, "rho_adapt must be 0 or 1");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");
@@ -171,12 +184,24 @@ static int column_rho(int K, const double* W, const double* rho, double w0_bot, 
     return LGK_OK;
 }
 
+static int ready(const lgk_result* r) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    return result_ready(*r->d);
+}
+
+static int case_free(const lgk_case* c) {
+    if (c->d->async_busy.load())
+        return fail(LGK_EINVAL, "case busy: an asynchronous solve of it is running (lgk_wait first)");
+    return LGK_OK;
+}
+
 int lgk_solve_weightings_masked(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
                                 double rho0, double tol, int max_iter, const uint32_t* mask,
                                 const double* q1_init, const double* q2_init, lgk_result** out) {
     if (!out) return fail(LGK_EINVAL, "out is NULL");
     *out = nullptr;
     if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
+    if (int rb = case_free(c)) return rb;
     if (K < 1 || K > 4096) return fail(LGK_EINVAL, "need 1 <= K <= 4096");
     if (!finite_nonneg(W, (size_t)K * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
     if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
@@ -224,17 +249,102 @@ int lgk_solve_weightings(lgk_case* c, int K, const double* W, const double* rho,
                                        nullptr, out);
 }
 
+int lgk_solve_weightings_async(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
+                               double rho0, double tol, int max_iter, lgk_result** out) {
+    if (!out) return fail(LGK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
+    if (K < 1 || K > 4096) return fail(LGK_EINVAL, "need 1 <= K <= 4096");
+    if (!finite_nonneg(W, (size_t)K * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
+    if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
+    std::vector<double> r;
+    int rrc = column_rho(K, W, rho, w0_bot, rho0, r);
+    if (rrc) return rrc;
+    int expect = 0;
+    if (!c->d->async_busy.compare_exchange_strong(expect, 1))
+        return fail(LGK_EINVAL, "case busy: an asynchronous solve of it is running (lgk_wait first)");
+    lgk_result* h = nullptr;
+    try {
+        std::vector<double> w(W, W + (size_t)K * 4);
+        std::unique_ptr<ResultData> res(new ResultData);
+        res->cs = c->d;
+        res->K = K;
+        res->tol = tol;
+        res->max_iter = max_iter;
+        res->running = true;
+        res->waited = false;
+        h = new lgk_result;
+        h->d = std::move(res);
+        ResultData* rd = h->d.get();
+        rd->worker = std::thread([rd, w = std::move(w), r = std::move(r)]() {
+            int rc = LGK_OK;
+            if (cudaSetDevice(rd->cs->device) != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(LGK_ECUDA, "cudaSetDevice failed in the solve thread");
+            } else {
+                try {
+                    rc = run_solve(*rd, w.data(), r.data(), nullptr, nullptr, nullptr);
+                } catch (const std::bad_alloc&) {
+                    rc = fail(LGK_ENOMEM, "host allocation failed");
+                }
+            }
+            rd->cs->async_busy = 0;
+            std::lock_guard<std::mutex> lk(rd->amu);
+            rd->async_rc = rc;
+            rd->async_err = rc ? g_err : std::string();
+            rd->running = false;
+            rd->acv.notify_all();
+        });
+    } catch (const std::exception&) {     // bad_alloc, or std::system_error from std::thread
+        c->d->async_busy = 0;
+        delete h;
+        return fail(LGK_ENOMEM, "could not start the solve thread");
+    }
+    *out = h;
+    return LGK_OK;
+}
+
+int lgk_wait(lgk_result* r, int timeout_ms) {
+    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (timeout_ms < 0) return fail(LGK_EINVAL, "timeout_ms must be >= 0");
+    ResultData& d = *r->d;
+    {
+        std::unique_lock<std::mutex> lk(d.amu);
+        if (!d.acv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !d.running; }))
+            return fail(LGK_ETIMEOUT, "solve still running after timeout_ms");
+    }
+    if (d.worker.joinable()) d.worker.join();
+    std::lock_guard<std::mutex> lk(d.amu);
+    if (d.async_rc) return fail(d.async_rc, d.async_err);
+    d.waited = true;
+    return LGK_OK;
+}
+
 int lgk_solve_stream(lgk_case* c, int K_total, const double* W, const double* rho, double w0_bot,
                      double rho0, double tol, int max_iter, int width, double* t, double* tau, int* iters,
                      double* obj, double* rel_pri, double* rel_dual, uint8_t* converged, double* prof_ms,
-                     long long* prof_launches) {
+                     long long* prof_launches, double* check) {
     if (!c || !W) return fail(LGK_EINVAL, "case or W is NULL");
+    if (int rb = case_free(c)) return rb;
     if (K_total < 1 || K_total > (1 << 20) || width < 1 || width > 4096)
         return fail(LGK_EINVAL, "need 1 <= K_total <= 2^20 and 1 <= width <= 4096");
     if (!finite_nonneg(W, (size_t)K_total * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
     if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
     if ((prof_ms || prof_launches) && !c->d->prm.profile)
         return fail(LGK_EINVAL, "profile outputs need lgk_params.profile = 1");
+    {
+        // The stream's iteration counter is a 32-bit int on the device.  A
+        // weighting holds its column for at most its cap rounded up to a graph
+        // replay plus one replay, and every column stays busy until the queue
+        // is empty, so the counter never passes
+        // (ceil(K_total / width) + 1) x (round_up(max_iter, replay) + replay).
+        const long long replay = 5LL * std::max(1, c->d->prm.check_every);
+        const long long per_w = round_up(max_iter, replay) + replay;
+        const long long rounds = (K_total + (long long)width - 1) / width + 1;
+        if ((double)rounds * (double)per_w > (double)(1 << 30))
+            return fail(LGK_EINVAL, "K_total / width x max_iter too large: the stream's iteration count "
+                                    "could pass 2^30; lower max_iter or K_total, or raise width");
+    }
     std::vector<double> r;
     int rc = column_rho(K_total, W, rho, w0_bot, rho0, r);
     if (rc) return rc;
@@ -261,6 +371,7 @@ int lgk_solve_stream(lgk_case* c, int K_total, const double* W, const double* rh
     ss.rel_pri = rel_pri;
     ss.rel_dual = rel_dual;
     ss.converged = converged;
+    ss.check = check;
     try {
         rc = run_solve(*res, W, r.data(), nullptr, nullptr, nullptr, &ss);
     } catch (const std::bad_alloc&) {
@@ -275,7 +386,7 @@ int lgk_solve_stream(lgk_case* c, int K_total, const double* W, const double* rh
 }
 
 int lgk_fetch_times(const lgk_result* r, double* t, double* tau) {
-    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (int rb = ready(r)) return rb;
     LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
     return fetch_times(*r->d, t, tau);
 }
@@ -284,6 +395,7 @@ int lgk_fetch_doses(const lgk_result* r, const double* phi_eval, int n_eval, dou
     if (!r || !phi_eval || !dose || n_eval < 1) return fail(LGK_EINVAL, "bad fetch_doses arguments");
     if (!finite_nonneg(phi_eval, (size_t)n_eval * r->d->cs->n_beams))
         return fail(LGK_EINVAL, "phi_eval must be finite and >= 0");
+    if (int rb = ready(r)) return rb;
     LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
     return fetch_doses(*r->d, phi_eval, n_eval, dose);
 }
@@ -291,6 +403,7 @@ int lgk_fetch_doses(const lgk_result* r, const double* phi_eval, int n_eval, dou
 int lgk_fetch_metrics(const lgk_result* r, const double* phi_eval, int n_eval, const int* label,
                       double* coverage, double* selectivity, double* gi, double* bot) {
     if (!r || !phi_eval || !label || n_eval < 1) return fail(LGK_EINVAL, "bad fetch_metrics arguments");
+    if (int rb = ready(r)) return rb;
     const CaseData& cs = *r->d->cs;
     if (!finite_nonneg(phi_eval, (size_t)n_eval * cs.n_beams))
         return fail(LGK_EINVAL, "phi_eval must be finite and >= 0");
@@ -303,19 +416,34 @@ int lgk_fetch_metrics(const lgk_result* r, const double* phi_eval, int n_eval, c
 
 int lgk_fetch_stats(const lgk_result* r, int* iters, double* obj, double* rel_pri, double* rel_dual,
                     uint8_t* converged) {
-    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (int rb = ready(r)) return rb;
     LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
     return fetch_stats(*r->d, iters, obj, rel_pri, rel_dual, converged);
 }
 
+int lgk_fetch_check(const lgk_result* r, double* out) {
+    if (!r || !out) return fail(LGK_EINVAL, "result or out is NULL");
+    if (int rb = ready(r)) return rb;
+    LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
+    ResultData& rd = *r->d;
+    if (rd.u64.empty()) return fail(LGK_EINVAL, "result holds no solve");
+    std::vector<int> cols(rd.K);
+    for (int j = 0; j < rd.K; ++j) cols[j] = j;
+    try {
+        return run_check(rd, cols.data(), rd.K, out);
+    } catch (const std::bad_alloc&) {
+        return fail(LGK_ENOMEM, "host allocation failed");
+    }
+}
+
 int lgk_fetch_state(const lgk_result* r, double* q1, double* q2) {
-    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (int rb = ready(r)) return rb;
     LGK_CUDA_TRY(cudaSetDevice(r->d->cs->device));
     return fetch_state(*r->d, q1, q2);
 }
 
 int lgk_fetch_profile(const lgk_result* r, double* ms, long long* launches) {
-    if (!r) return fail(LGK_EINVAL, "result is NULL");
+    if (int rb = ready(r)) return rb;
     if (!r->d->cs->prm.profile) return fail(LGK_EINVAL, "solve was not profiled (lgk_params.profile = 0)");
     for (int k = 0; k < LGK_K_COUNT; ++k) {
         if (ms) ms[k] = r->d->prof_ms[k];

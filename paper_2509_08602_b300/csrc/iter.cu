@@ -33,6 +33,10 @@
 namespace lgk {
 
 ResultData::~ResultData() {
+    if (worker.joinable()) {      // an asynchronous solve still running: stop it at its next replay
+        cancel = true;
+        worker.join();
+    }
     if (cs && cs->stream) cudaStreamSynchronize(cs->stream);
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
@@ -414,6 +418,42 @@ __global__ void k_reset_cols(IterCtx cx, const int* __restrict__ cols, void* R1,
     }
 }
 
+// Penalty change of the listed columns (residual balancing): rho_j was
+// multiplied by f = fac[c] (colp already holds the new rho and 1/rho).  The
+// projections z = P(q) stay, the scaled duals y = q - z become y / f (the
+// multipliers rho y are unchanged), and R1 = 2 P1(q1) - q1 - c/rho is rebuilt
+// for the next GEMM1 with the new q1 and rho.
+template <bool BF16>
+__global__ void k_rescale_cols(IterCtx cx, const int* __restrict__ cols, const float* __restrict__ fac,
+                               void* R1) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y, j = cols[c];
+    const float inv_f = 1.0f / fac[c];
+    if (e < cx.n_pad) {
+        const size_t o = (size_t)j * cx.n_pad + e;
+        const int sl = cx.col_slot[e];
+        const float u = u_at(cx, e, sl, j);
+        const float q = cx.q1[o];
+        const float z = fminf(fmaxf(q, 0.f), u);
+        const float qn = z + (q - z) * inv_f;
+        cx.q1[o] = qn;
+        const float r = 2.f * z - qn - cx.c_slot[sl] * cx.inv_rho[j];
+        if (BF16) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(r, hi, lo);
+            static_cast<__nv_bfloat16*>(R1)[o] = hi;
+            static_cast<__nv_bfloat16*>(R1)[(size_t)cx.Kp * cx.n_pad + o] = lo;
+        } else {
+            static_cast<float*>(R1)[o] = r;
+        }
+    }
+    if (e < cx.m_pad) {
+        const size_t o = (size_t)j * cx.m_pad + e;
+        const float q = cx.q2[o];
+        const float z = fminf(q, b_of(e, j, cx.n_beams, cx.m, cx.Dr, cx.wbot));
+        cx.q2[o] = z + (q - z) * inv_f;
+    }
+}
+
 // q1 (K x n) and q2 (K x m) of the q-form state, FP64.
 __global__ void k_state(IterCtx cx, int K, double* q1, double* q2) {
     int e = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -595,21 +635,25 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
 
     // per-column tables (Appendix A bounds; Eq. rho_rule or caller rho)
     std::vector<float> utab((size_t)Kp * S + S, 0.0f), colp((size_t)4 * Kp, 0.0f);
+    r.u64.assign((size_t)Kp * S, 0.0);
+    r.wb64.assign(Kp, 0.0);
     // column j's tables for weights w = (w_T, w_R, w_LD, w_BOT), penalty rh and
     // per-slot point counts nc
     auto fill_col = [&](int j, const double* w, double rh, const int* nc) {
         const double wT = w[0], wR = w[1], wLD = w[2], wB = w[3];
-        float* u = &utab[(size_t)j * S];
+        double* u = &r.u64[(size_t)j * S];
         for (int k = 0; k < T; ++k) {
-            u[3 * k] = nc[3 * k] ? (float)(cs.q_area[k] * wT / nc[3 * k]) : 0.f;
-            u[3 * k + 1] = nc[3 * k + 1] ? (float)(cs.q_vol[k] * wT / nc[3 * k + 1]) : 0.f;
-            u[3 * k + 2] = nc[3 * k + 2] ? (float)((wR / T) / nc[3 * k + 2]) : 0.f;
+            u[3 * k] = nc[3 * k] ? cs.q_area[k] * wT / nc[3 * k] : 0.0;
+            u[3 * k + 1] = nc[3 * k + 1] ? cs.q_vol[k] * wT / nc[3 * k + 1] : 0.0;
+            u[3 * k + 2] = nc[3 * k + 2] ? (wR / T) / nc[3 * k + 2] : 0.0;
         }
-        u[slot_ld1(T)] = nc[slot_ld1(T)] ? (float)(wLD / nc[slot_ld1(T)]) : 0.f;
-        u[slot_ld2(T)] = nc[slot_ld2(T)] ? (float)(wLD / nc[slot_ld2(T)]) : 0.f;
+        u[slot_ld1(T)] = nc[slot_ld1(T)] ? wLD / nc[slot_ld1(T)] : 0.0;
+        u[slot_ld2(T)] = nc[slot_ld2(T)] ? wLD / nc[slot_ld2(T)] : 0.0;
         u[slot_oar(T)] = INFINITY;
         u[slot_bot(T)] = INFINITY;
-        u[slot_pad(T)] = 0.f;
+        u[slot_pad(T)] = 0.0;
+        for (int s = 0; s < S; ++s) utab[(size_t)j * S + s] = (float)u[s];
+        r.wb64[j] = wB;
         colp[j] = (float)rh;
         colp[Kp + j] = (float)(1.0 / rh);
         colp[2 * Kp + j] = (float)wB;
@@ -778,6 +822,12 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             LGK_CUDA_TRY(cudaMemcpyAsync(stv.data(), r.stats.p, stv.size() * 8, cudaMemcpyDeviceToHost, st));
             LGK_CUDA_TRY(cudaMemcpyAsync(lam.data(), lam_d.p, lam.size() * 8, cudaMemcpyDeviceToHost, st));
             LGK_CUDA_TRY(cudaStreamSynchronize(st));
+            std::vector<double> chk;
+            if (ss.check) {     // FP64 check of the stopped columns, before they are refilled
+                chk.resize(ret.size() * (size_t)LGK_CHECK_COUNT);
+                const int rcc = run_check(r, ret.data(), (int)ret.size(), chk.data());
+                if (rcc) return rcc;
+            }
             // graph slots assume replays that start on a multiple of their
             // length; the counter stops early only once no column runs
             hc->iter = (int)round_up(hc->iter, per_graph);
@@ -789,6 +839,9 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
                 if (ss.rel_pri) ss.rel_pri[w] = stv[j];
                 if (ss.rel_dual) ss.rel_dual[w] = stv[(size_t)Kp + j];
                 if (ss.converged) ss.converged[w] = (uint8_t)(a[(size_t)Kp + j] != 0);
+                if (ss.check)
+                    std::copy(&chk[c * LGK_CHECK_COUNT], &chk[c * LGK_CHECK_COUNT] + LGK_CHECK_COUNT,
+                              ss.check + (size_t)w * LGK_CHECK_COUNT);
                 const double* l = &lam[c * (size_t)cs.m];
                 if (ss.t) std::copy(l, l + cs.n_beams, ss.t + (size_t)w * cs.n_beams);
                 if (ss.tau) std::copy(l + cs.n_beams, l + cs.m, ss.tau + (size_t)w * cs.n_iso);
@@ -831,6 +884,57 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             }
         return LGK_OK;
     };
+    // residual balancing (lgk_params.rho_adapt) at a replay boundary: columns
+    // still running whose last residual test is this replay's get rho x 1.5
+    // or / 1.5 when one relative residual exceeds 3 times the other (at most
+    // 40 changes per column; a column refilled by a stream starts afresh)
+    std::vector<int> rho_changes(Kp, 0), adapt_start(Kp, -1);
+    DevBuf adapt_d;
+    auto adapt_rho = [&]() -> int {
+        std::vector<int> a(Kp);
+        std::vector<double> stv(2 * (size_t)Kp);
+        LGK_CUDA_TRY(cudaMemcpyAsync(a.data(), r.active.p, (size_t)Kp * 4, cudaMemcpyDeviceToHost, st));
+        LGK_CUDA_TRY(cudaMemcpyAsync(stv.data(), r.stats.p, stv.size() * 8, cudaMemcpyDeviceToHost, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int> cols;
+        std::vector<float> fac;
+        for (int j = 0; j < Kp; ++j) {
+            if (!a[j]) continue;
+            const int start = stream ? start_it[j] : 0;
+            if (adapt_start[j] != start) {          // a new weighting in this column
+                adapt_start[j] = start;
+                rho_changes[j] = 0;
+            }
+            if (hc->iter <= start || rho_changes[j] >= 40) continue;   // no test of its own yet
+            const double rp = stv[j], rd = stv[(size_t)Kp + j];
+            float f;
+            if (rp > 3.0 * rd) f = 1.5f;
+            else if (rd > 3.0 * rp) f = 1.0f / 1.5f;
+            else continue;
+            colp[j] *= f;
+            colp[(size_t)Kp + j] = 1.0f / colp[j];
+            ++rho_changes[j];
+            cols.push_back(j);
+            fac.push_back(f);
+        }
+        if (cols.empty()) return LGK_OK;
+        if (!adapt_d.p) {
+            const int rc2 = adapt_d.alloc((size_t)Kp * 8);
+            if (rc2) return rc2;
+        }
+        int* cols_a = adapt_d.as<int>();
+        float* fac_a = reinterpret_cast<float*>(cols_a + Kp);
+        LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), (size_t)2 * Kp * 4, cudaMemcpyHostToDevice, st));
+        LGK_CUDA_TRY(cudaMemcpyAsync(cols_a, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, st));
+        LGK_CUDA_TRY(cudaMemcpyAsync(fac_a, fac.data(), fac.size() * 4, cudaMemcpyHostToDevice, st));
+        const int ne = std::max(cs.n_pad, cs.m_pad);
+        dim3 g((ne + 255) / 256, (unsigned)cols.size());
+        if (bf16) k_rescale_cols<true><<<g, 256, 0, st>>>(cx, cols_a, fac_a, r.R1.p);
+        else k_rescale_cols<false><<<g, 256, 0, st>>>(cx, cols_a, fac_a, r.R1.p);
+        LGK_LAUNCH_CHECK();
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        return LGK_OK;
+    };
     int iter_before = 0;
     auto t0 = std::chrono::steady_clock::now();
     rc = LGK_OK;
@@ -855,6 +959,11 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         if (hc->err) {
             set_error("device error flag " + std::to_string(hc->err) + " raised during the solve");
             rc = LGK_ECUDA;
+            break;
+        }
+        if (r.cancel.load()) {
+            set_error("solve cancelled (its result was freed while it ran)");
+            rc = LGK_ETIMEOUT;
             break;
         }
         if (!r.prof_ev.empty()) {       // iterations of this replay that did work
@@ -882,6 +991,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         } else if (hc->n_active == 0) {
             break;
         }
+        if (cs.prm.rho_adapt && (rc = adapt_rho())) break;
         if (r.refine && cs.prm.lo_refresh_iters > 0 && age >= cs.prm.lo_refresh_iters) {
             // columns still running this long: continue with the literal
             // iteration (all terms every step) from the current state

@@ -3,7 +3,12 @@
 
 #include <cublas_v2.h>
 
+#include <atomic>
+#include <condition_variable>
 #include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "lgk_common.cuh"
@@ -48,6 +53,7 @@ struct CaseData {
     DevBuf G32;        // float [m_pad][m_pad] S^{-1}    (LGK_PREC_FP32)
     DevBuf G3;         // bf16 [3][m_pad][m_pad] S^{-1} = hi + mid + lo (BF16 forms)
     DevBuf ctrl_setup; // int [4] device error flags during set-up
+    std::atomic<int> async_busy{0};   // an asynchronous solve of this case is running
     size_t bytes_held() const;
     ~CaseData();
 };
@@ -100,6 +106,20 @@ struct ResultData {
     DevBuf ctrl;              // Control
     DevBuf resid;             // double [n_resid_blocks][Kp][5] residual partial sums
     DevBuf stats;             // double [3][Kp]: rel_pri, rel_dual, obj
+    std::vector<double> u64;  // host [Kp][n_slot]: each column's bounds u in FP64 (the FP64 check)
+    std::vector<double> wb64; // host [Kp]: each column's w_BOT in FP64
+    DevBuf chk;               // device temporaries of the FP64 check (run_check)
+
+    // asynchronous solve (lgk_solve_weightings_async): the worker thread that
+    // runs it, its outcome, and a cancel request checked between graph replays
+    std::thread worker;
+    std::mutex amu;
+    std::condition_variable acv;
+    bool running = false;
+    bool waited = true;       // false from the async start until lgk_wait succeeds
+    int async_rc = LGK_OK;
+    std::string async_err;
+    std::atomic<bool> cancel{false};
     int n_resid_n = 0, n_resid_m = 0;     // residual partial blocks from the n- and m-blocks
 
     cudaGraphExec_t graph = nullptr;
@@ -126,6 +146,7 @@ struct StreamSpec {
     double *t = nullptr, *tau = nullptr, *obj = nullptr, *rel_pri = nullptr, *rel_dual = nullptr;
     int* iters = nullptr;
     uint8_t* converged = nullptr;
+    double* check = nullptr;         // K_total x LGK_CHECK_COUNT (FP64 check per weighting)
 };
 
 // one solve (iter.cu); with `stream`, W and rho hold its first r.K weightings
@@ -139,6 +160,10 @@ int fetch_state(const ResultData& r, double* q1, double* q2);
 int times_into(const ResultData& r, double* t_dev);   // K x n_beams FP64, device
 int fetch_metrics(const ResultData& r, const double* phi_eval, int n_eval, const int* label,
                   double* coverage, double* selectivity, double* gi, double* bot);
+// 0 when a result may be read (its asynchronous solve, if any, waited for)
+int result_ready(ResultData& d);
+// FP64 check of the listed columns (check.cu): out [nc][LGK_CHECK_COUNT], host
+int run_check(ResultData& r, const int* cols, int nc, double* out);
 
 // FP64 GEMM (setup.cu):  C = alpha op(A) op(B) + beta C, row-major.
 int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,

@@ -27,16 +27,31 @@ constexpr int kMaxDevices = 64;
 static double* g_scratch_addr[kMaxDevices] = {};
 static std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device `dev`, looked up
-// once per device.  Host code only holds a stand-in for the symbol; the
-// device address must come from the runtime.
-static int scratch_address(int dev, double** out) {
+// Device address of the scratch array on the current device `dev`.  Host
+// code only holds a stand-in for the symbol; the device address must come
+// from the runtime.  The first call on a device looks it up (this may load
+// the library's module on that device, so it must not happen during a stream
+// capture).  Later calls look it up again whenever `st` is not capturing, so
+// that an address cached before a device reset (which unloads the module and
+// may place the array elsewhere when it is reloaded) is never used; during a
+// capture they use the cached address.
+static int scratch_address(int dev, cudaStream_t st, double** out) {
     if (dev < 0 || dev >= kMaxDevices) {
         set_error("device ordinal out of range for the static scratch table");
         return LGK_EINVAL;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    if (!g_scratch_addr[dev] || cap == cudaStreamCaptureStatusNone) {
+        if (cap != cudaStreamCaptureStatusNone) {
+            set_error("lgk_fetch_doses_device: the first call on a device must not be made during a "
+                      "stream capture");
+            return LGK_EINVAL;
+        }
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_times_scratch);
         if (e != cudaSuccess || !p) {
@@ -48,6 +63,20 @@ static int scratch_address(int dev, double** out) {
     *out = g_scratch_addr[dev];
     return LGK_OK;
 }
+
+// Restores the caller's current device when the entry point returns.
+struct DeviceGuard {
+    int prev = -1;
+    DeviceGuard() {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 // True if p is device memory of device `dev` (or managed memory).
 static bool on_device(const void* p, int dev) {
@@ -68,6 +97,7 @@ extern "C" int lgk_fetch_doses_device(const lgk_result* res, const double* phi_e
         set_error("lgk_fetch_doses_device: NULL result/buffer or n_eval < 1");
         return LGK_EINVAL;
     }
+    if (int rb = result_ready(*res->d)) return rb;
     const ResultData& r = *res->d;
     CaseData& cs = *r.cs;
     const long long need = (long long)r.K * cs.n_beams;
@@ -77,6 +107,7 @@ extern "C" int lgk_fetch_doses_device(const lgk_result* res, const double* phi_e
                   std::to_string(LGK_NOALLOC_MAX_TIMES) + " doubles; split the plans");
         return LGK_EINVAL;
     }
+    DeviceGuard keep_device;
     LGK_CUDA_TRY(cudaSetDevice(cs.device));
     if (!on_device(phi_eval_dev, cs.device) || !on_device(dose_dev, cs.device)) {
         set_error("lgk_fetch_doses_device: phi_eval_dev and dose_dev must be device memory of the "
@@ -85,7 +116,7 @@ extern "C" int lgk_fetch_doses_device(const lgk_result* res, const double* phi_e
     }
     double* t = nullptr;
     int rc;
-    if ((rc = scratch_address(cs.device, &t))) return rc;
+    if ((rc = scratch_address(cs.device, cs.stream, &t))) return rc;
     if ((rc = times_into(r, t))) return rc;
     // dose[K][E] = t[K][B] . phi_eval[E][B]^T, the kernel lgk_fetch_doses uses
     if ((rc = dgemm(cs.stream, false, true, r.K, n_eval, cs.n_beams, 1.0, t, cs.n_beams, phi_eval_dev,

@@ -213,6 +213,7 @@ int lgk_low_dose_volumes(const lgk_result* res, const double* phi_cand, int n_ca
     for (int l = 0; l < n_levels; ++l)
         if (!(d_lo[l] > 0) || !(delta[l] > 0) || !isfinite(d_lo[l] + delta[l]))
             return fail2(LGK_EINVAL, "lgk_low_dose_volumes: need d_lo > 0 and delta > 0");
+    if (int rb = result_ready(*res->d)) return rb;
     const CaseData& cs = *res->d->cs;
     if (!all_finite_nonneg(phi_cand, (size_t)n_cand * cs.n_beams))
         return fail2(LGK_EINVAL, "lgk_low_dose_volumes: phi_cand must be finite and >= 0");

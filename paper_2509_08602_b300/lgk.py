@@ -43,7 +43,8 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("normalize_rows", C.c_int), ("scale_bot", C.c_int),
                 ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
-                ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int)]
+                ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int),
+                ("rho_adapt", C.c_int)]
 
 
 class ServerParams(C.Structure):
@@ -89,8 +90,17 @@ def _load():
     lib.lgk_solve_stream.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double), C.c_double,
                                      C.c_double, C.c_double, C.c_int, C.c_int, P(C.c_double),
                                      P(C.c_double), P(C.c_int), P(C.c_double), P(C.c_double),
-                                     P(C.c_double), P(C.c_uint8), P(C.c_double), P(C.c_longlong)]
+                                     P(C.c_double), P(C.c_uint8), P(C.c_double), P(C.c_longlong),
+                                     P(C.c_double)]
     lib.lgk_solve_stream.restype = C.c_int
+    lib.lgk_fetch_check.argtypes = [C.c_void_p, P(C.c_double)]
+    lib.lgk_fetch_check.restype = C.c_int
+    lib.lgk_solve_weightings_async.argtypes = [C.c_void_p, C.c_int, P(C.c_double), P(C.c_double),
+                                               C.c_double, C.c_double, C.c_double, C.c_int,
+                                               P(C.c_void_p)]
+    lib.lgk_solve_weightings_async.restype = C.c_int
+    lib.lgk_wait.argtypes = [C.c_void_p, C.c_int]
+    lib.lgk_wait.restype = C.c_int
     lib.lgk_low_dose_volumes.argtypes = [C.c_void_p, P(C.c_double), C.c_int, C.c_int, P(C.c_double),
                                          P(C.c_double), P(C.c_uint32), P(C.c_int)]
     lib.lgk_sample_low_dose.argtypes = [C.c_int, C.c_int, P(C.c_uint32), P(C.c_int), C.c_uint64,
@@ -230,14 +240,39 @@ def solve_weightings(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: floa
     return Result(h, K, case)
 
 
+def solve_weightings_async(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 0.0,
+                           tol: float = 1e-4, max_iter: int = 10000) -> Result:
+    """lgk_solve_weightings_async: starts the solve and returns its Result at
+    once; call wait(res, timeout_ms) before fetching from it."""
+    W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+    K = W.shape[0]
+    r = None if rho is None else np.ascontiguousarray(np.broadcast_to(rho, (K,)), dtype=np.float64)
+    h = C.c_void_p()
+    _check(_lib.lgk_solve_weightings_async(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double),
+                                           float(w0_bot), float(rho0), float(tol), int(max_iter),
+                                           C.byref(h)))
+    return Result(h, K, case)
+
+
+def wait(res: Result, timeout_ms: int) -> bool:
+    """lgk_wait: True once the solve finished (raises LgkError if it failed),
+    False if it is still running after timeout_ms."""
+    rc = _lib.lgk_wait(res._h, int(timeout_ms))
+    if rc == 6:
+        return False
+    _check(rc)
+    return True
+
+
 def solve_stream(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 0.0,
                  tol: float = 1e-4, max_iter: int = 10000, width: int = 32,
-                 profile: bool = False) -> dict:
+                 profile: bool = False, check: bool = False) -> dict:
     """lgk_solve_stream: the K_total weightings of W run through `width`
     columns, each freed column taking the next weighting.  Returns, per
     weighting in W's order, t (K_total x 24N), tau (K_total x N), iters, obj,
     rel_pri, rel_dual, converged; with profile=True (the case created with
-    profile=1) also {kernel: (ms, launches)} under "profile"."""
+    profile=1) also {kernel: (ms, launches)} under "profile"; with check=True
+    the FP64 check of each weighting (as fetch_check) under "check"."""
     W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
     if W.shape[1] != 4:
         raise LgkError(1, "W must be K x 4")
@@ -251,12 +286,15 @@ def solve_stream(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 
     conv = np.empty(K, np.uint8)
     ms = np.zeros(len(KERNELS)) if profile else None
     nl = np.zeros(len(KERNELS), np.int64) if profile else None
+    ck = np.full((K, len(CHECK_FIELDS)), np.nan) if check else None
     _check(_lib.lgk_solve_stream(case._h, K, _ptr(W, C.c_double), _ptr(r, C.c_double), float(w0_bot),
                                  float(rho0), float(tol), int(max_iter), int(width), _ptr(t, C.c_double),
                                  _ptr(tau, C.c_double), _ptr(it, C.c_int), _ptr(obj, C.c_double),
                                  _ptr(rp, C.c_double), _ptr(rd, C.c_double), _ptr(conv, C.c_uint8),
-                                 _ptr(ms, C.c_double), _ptr(nl, C.c_longlong)))
+                                 _ptr(ms, C.c_double), _ptr(nl, C.c_longlong), _ptr(ck, C.c_double)))
     out = dict(t=t, tau=tau, iters=it, obj=obj, rel_pri=rp, rel_dual=rd, converged=conv.astype(bool))
+    if check:
+        out["check"] = {k: ck[:, i].copy() for i, k in enumerate(CHECK_FIELDS)}
     if profile:
         out["profile"] = {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(KERNELS)}
     return out
@@ -422,6 +460,17 @@ def fetch_stats(res: Result) -> dict:
     _check(_lib.lgk_fetch_stats(res._h, _ptr(it, C.c_int), _ptr(obj, C.c_double), _ptr(rp, C.c_double),
                                 _ptr(rd, C.c_double), _ptr(conv, C.c_uint8)))
     return dict(iters=it, obj=obj, rel_pri=rp, rel_dual=rd, converged=conv.astype(bool))
+
+
+CHECK_FIELDS = ("obj", "plan", "gap", "infeas", "infeas_abs", "hard", "bound")   # LGK_CHECK_*
+
+
+def fetch_check(res: Result) -> dict:
+    """lgk_fetch_check: the FP64 check of every plan, {field: (K,) array}
+    with the fields of CHECK_FIELDS (LGK_CHECK_* in include/lgk.h)."""
+    out = np.empty((res.K, len(CHECK_FIELDS)))
+    _check(_lib.lgk_fetch_check(res._h, _ptr(out, C.c_double)))
+    return {k: out[:, i].copy() for i, k in enumerate(CHECK_FIELDS)}
 
 
 def fetch_state(res: Result):

@@ -1,0 +1,105 @@
+"""Write the stored oracle plans for the full-size GPU tests.
+
+Calls only the oracle (`oracle/`) and the seeded input generator (`synth/`):
+for a sample of slider weightings of the 3750 x 41200 case (81 weightings)
+and of the 5000 x 61600 case (441 weightings) it runs the FP64 literal ADMM
+of Eq. admm to relative residual 1e-6 (100 times tighter than the device's
+1e-4 stop), evaluates the plans' clinical metrics on a regular grid
+(Sec. 3.B conventions), the weighted-sum objective of Sec. 2.A at the plans'
+multipliers (the LP's dual objective: weak duality brackets the optimum
+between it and c^T z1), and stores them as JSON.
+
+    python tests/golden/make_full_size.py --cfg 1     # about an hour on 8 cores
+    python tests/golden/make_full_size.py --cfg 2
+
+The sampled weightings (indices into `synth.cases.slider_weights(grid)`,
+row-major over (s_LD, s_BOT)) are the four corners of the slider grid, its
+centre and one off-centre point; index 0 (s_LD = s_BOT = 0, the lowest BOT
+weight) converges slowest.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import admm as AD          # noqa: E402
+from oracle import kkt as KK           # noqa: E402
+from oracle import lp as L             # noqa: E402
+from oracle import metrics as M        # noqa: E402
+from synth import cases as SC          # noqa: E402
+
+TOL = 1e-6
+GRID_SPACING = {1: 2.0, 2: 2.0}        # mm
+GRID_MARGIN = 12.0                     # mm
+
+
+def sample_indices(g: int) -> list[int]:
+    c = g // 2
+    return sorted({0, g - 1, g * (g - 1), g * g - 1, c * g + c, (c // 2) * g + c // 2})
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--cfg", type=int, required=True, choices=(1, 2))
+    ap.add_argument("--max-iter", type=int, default=400000)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    out = a.out or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                f"full_size_cfg{a.cfg}.json")
+    t0 = time.time()
+    case = SC.workload_case(a.cfg)
+    g = SC.WORKLOADS[a.cfg]["grid"]
+    idx = sample_indices(g)
+    W = SC.slider_weights(g)[idx]
+    lp = L.precondition(L.assemble_case(case))
+    rho0 = L.rho0_for(lp)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, rho0)
+    b, l, u = L.bounds(lp, W)
+    print(f"cfg{a.cfg}: A {lp.m} x {lp.n}, beta {lp.beta:.3f}, K {len(idx)}; "
+          f"set-up {time.time() - t0:.0f} s", flush=True)
+    res = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=a.max_iter, tol=TOL)
+    print(f"ADMM {time.time() - t0:.0f} s, iterations {res.iters.tolist()}, "
+          f"converged {res.converged.tolist()}", flush=True)
+    lam = res.multipliers()                       # scaled multipliers rho y2 (m x K)
+    t, tau = L.times_from_multipliers(lp, lam)
+    pts, label, _ = SC.eval_grid(case, spacing=GRID_SPACING[a.cfg], margin=GRID_MARGIN)
+    phi_eval = SC.dose_rate(pts, case.iso)
+    d = M.dose(phi_eval, t)
+    met = M.plan_metrics(d, label, case.d_presc, t, case.n_iso)
+    rows = []
+    for c, w in enumerate(idx):
+        primal = float(lp.c @ res.z1[:, c])
+        plan_obj, viol = KK.planning_objective(lp.A, b[:, c], lp.c, u[:, c], lam[:, c])
+        rows.append(dict(
+            index=int(w), W=W[c].tolist(), rho=float(rho[c]), iters=int(res.iters[c]),
+            converged=bool(res.converged[c]), rel_pri=float(res.rel_pri[c]),
+            rel_dual=float(res.rel_dual[c]), obj=primal, planning_objective=plan_obj,
+            hard_violation=viol, max_lam=float(np.abs(lam[:, c]).max()),
+            gap=abs(primal + plan_obj) / max(1.0, abs(primal)),
+            coverage=float(met["coverage"][c]), selectivity=float(met["selectivity"][c]),
+            gi=None if np.isnan(met["gi"][c]) else float(met["gi"][c]),
+            bot=float(met["bot"][c])))
+        print(rows[-1], flush=True)
+    doc = dict(
+        workload=SC.WORKLOADS[a.cfg]["name"], cfg=a.cfg, m=lp.m, n=lp.n, beta=lp.beta,
+        rho0=rho0, w0_bot=SC.W0_BOT, tol=TOL, grid=g,
+        eval_grid=dict(spacing=GRID_SPACING[a.cfg], margin=GRID_MARGIN, points=int(pts.shape[0])),
+        method="oracle.admm.admm (FP64 literal ADMM, Eq. admm) to relative residual 1e-6; "
+               "metrics by oracle.metrics.plan_metrics; planning objective by "
+               "oracle.kkt.planning_objective",
+        seconds=round(time.time() - t0, 1), plans=rows)
+    with open(out, "w") as f:
+        json.dump(doc, f, indent=1)
+    print("wrote", out, flush=True)
+
+
+if __name__ == "__main__":
+    main()

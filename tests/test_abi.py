@@ -95,7 +95,10 @@ def test_null_arguments_are_errors_not_crashes(lgk):
     assert lib.lgk_solve_weightings_masked(None, 1, None, None, 0.0, 0.0, 0.0, 1, None, None, None,
                                            ctypes.byref(h)) == 1
     assert lib.lgk_solve_stream(None, 1, None, None, 0.0, 0.0, 0.0, 1, 1, None, None, None, None, None,
-                                None, None, None, None) == 1
+                                None, None, None, None, None) == 1
+    assert lib.lgk_fetch_check(None, None) == 1
+    assert lib.lgk_solve_weightings_async(None, 1, None, None, 0.0, 0.0, 0.0, 1, ctypes.byref(h)) == 1
+    assert lib.lgk_wait(None, 0) == 1
     lib.lgk_free_result(None)
     lib.lgk_destroy_case(None)
     assert b"NULL" in lib.lgk_last_error() or len(lib.lgk_last_error()) > 0

@@ -27,6 +27,8 @@ from oracle import metrics as M
 from oracle import simplex as SX
 from synth import cases as SC
 
+from device_model import lagged_admm
+
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
@@ -130,8 +132,8 @@ def test_short_trajectory_from_zero(lgk, cfg0, prec):
 def test_lagged_low_term_trajectory(lgk, cfg0):
     """The default two-term iteration (lo_refresh = 1): light steps with A_hi
     plus the low term's products from the last full step.  25 iterations from
-    zero (full at 1, 10, 20) against the oracle's lagged variant on the same
-    two-term matrix; the bound is 25 one-step bounds."""
+    zero (full at 1, 10, 20) against the test-side model of that iteration
+    (`device_model.lagged_admm`) on the same two-term matrix; the bound is 25 one-step bounds."""
     c = cfg0
     cs = make(lgk, c["case"], 2)
     lp = c["lp"]
@@ -140,7 +142,7 @@ def test_lagged_low_term_trajectory(lgk, cfg0):
     tol = 25 * np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, 2, A.shape[1])
     res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=25)
     g1, g2 = lgk.fetch_state(res)
-    o = AD.admm(A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=25, lagged_lo=(hi, 10, 0))
+    o = lagged_admm(A, hi, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=25, refresh=10)
     r1, r2 = o.z1 + o.y1, o.z2 + o.y2
     assert np.abs(g1.T - r1).max() <= tol * np.abs(r1).max()
     assert np.abs(g2.T - r2).max() <= tol * np.abs(r2).max()
@@ -433,3 +435,40 @@ def test_stream_width_one_and_iteration_cap(lgk, cfg0):
     assert not s["converged"].any()
     assert np.all((s["iters"] >= 60) & (s["iters"] < 110)), s["iters"]
     assert np.isfinite(s["t"]).all() and (s["t"] >= 0).all()
+
+
+def test_adaptive_rho_converged_parity(lgk, cfg0):
+    """Per-column residual balancing (lgk_params.rho_adapt = 1; Sec. 3.C allows
+    a penalty per weighting because S = A A^T + I does not depend on it)
+    against the oracle's ADMM with the same rule (oracle.admm balance = (50,
+    3, 1.5, 40): every 50 iterations, factor 1.5 when one relative residual
+    exceeds 3 times the other, at most 40 changes).  The penalty paths may
+    part where a ratio sits at the threshold (FP32 against FP64 residuals),
+    so the gates are those of any converged plan: every weighting converges,
+    objective within 1e-3 of the simplex optimum, residuals <= 1e-4, and
+    coverage, selectivity, GI and BOT within 0.5 % of the oracle's balanced
+    plan.  The balanced solve must not need more iterations on average than
+    the fixed-penalty one."""
+    c = cfg0
+    case, lp = c["case"], c["lp"]
+    ref = AD.admm(lp.A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=TOL,
+                  balance=(50, 3.0, 1.5, 40))
+    assert ref.converged.all()
+    t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
+    met_ref = M.plan_metrics(M.dose(c["phi_eval"], t_ref), c["label"], case.d_presc, t_ref, case.n_iso)
+    cs = make(lgk, case, 2, rho_adapt=1)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all()
+    gap = np.abs(st["obj"] - c["opt"]) / np.maximum(1.0, np.abs(c["opt"]))
+    assert gap.max() <= 1e-3, gap
+    assert st["rel_pri"].max() <= TOL and st["rel_dual"].max() <= TOL
+    t, _ = lgk.fetch_times(res)
+    dose = lgk.fetch_doses(res, c["phi_eval"])
+    met = M.plan_metrics(dose.T, c["label"], case.d_presc, t.T, case.n_iso)
+    for key in ("coverage", "selectivity", "gi", "bot"):
+        rel = np.abs(met[key] - met_ref[key]) / np.abs(met_ref[key])
+        assert rel.max() <= 5e-3, (key, rel)
+    fixed = lgk.fetch_stats(lgk.solve_weightings(make(lgk, case, 2), c["W"], c["rho"], tol=TOL,
+                                                 max_iter=20000))
+    assert st["iters"].mean() <= fixed["iters"].mean(), (st["iters"], fixed["iters"])

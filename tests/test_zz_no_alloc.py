@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import lp as L
+from oracle import metrics as M
 from synth import cases as SC
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +53,27 @@ def test_device_doses_match_fetch_doses_on_two_calls_in_a_row(env):
         # same FP64 kernel on the same sector times: the tolerance of the
         # dose check in the parity tests
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+        # and the oracle's dose d = Phi_eval t (FP64 on the host) from the
+        # plans' sector times
+        t, _ = lgk.fetch_times(res)
+        np.testing.assert_allclose(got, M.dose(phi_eval, t.T).T, rtol=1e-12, atol=1e-12)
+
+
+def test_device_doses_allocate_nothing(env):
+    """The property the entry point exists for: after its first call on the
+    device (which looks up the scratch array), a call leaves the device's
+    free memory unchanged."""
+    torch, lgk, cs, W, rho, phi_eval = env
+    res = lgk.solve_weightings(cs, W[:3], rho[:3], tol=0.0, max_iter=20)
+    phi_d = torch.from_numpy(phi_eval).to("cuda:0")
+    out = torch.empty((3, phi_eval.shape[0]), dtype=torch.float64, device="cuda:0")
+    torch.cuda.synchronize()
+    lgk.fetch_doses_device(res, phi_d.data_ptr(), phi_eval.shape[0], out.data_ptr())
+    free0, _ = torch.cuda.mem_get_info(0)
+    for _ in range(3):
+        lgk.fetch_doses_device(res, phi_d.data_ptr(), phi_eval.shape[0], out.data_ptr())
+    free1, _ = torch.cuda.mem_get_info(0)
+    assert free1 == free0, (free0, free1)
 
 
 def test_device_doses_reject_host_buffers_and_oversized_batches(env):
