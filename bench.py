@@ -174,6 +174,11 @@ def allreduce_sum(x, world):
     return float(t.item())
 
 
+def knobs(args):
+    """lgk_params fields the command line sets for every BF16 case."""
+    return dict(solve_refine=args.solve_refine, setup_fp64=int(args.setup_fp64), rho_adapt=int(args.rho_adapt))
+
+
 def passes(st, ck, tol):
     """Plans counted as converged: the device's residual test passed (relative
     residuals <= tol) and the FP64 check of the plan against its exact LP
@@ -290,6 +295,9 @@ def workload_config(case, W, args):
                 "; between residual tests (every 10 iterations) the heavy products use A's high term "
                 "and add the low term's products from the last test iteration (lo_refresh)"
                 if args.precision == "bf16x3" and not args.exact else ""),
+            "solve_refine": args.solve_refine, "rho_adapt": bool(args.rho_adapt),
+            "schur": "S = I + A A^T on " + ("FP64 CUDA cores" if args.setup_fp64 else "tensor cores (BF16 "
+                                             "products, FP32 chunk sums, FP64 across chunks)"),
             "rho": "Eq. rho_rule, rho0 = 1100 beta", "l2": "inputs larger than L2 (A resident, "
             f"{A_BYTES[args.precision] * m * n / 1e6:.0f} MB > 126 MB)", "parallelism": "replicas"}
 
@@ -332,7 +340,7 @@ def run_ours(args, rank, world, local):
     # iteration graph and stop consecutive kernels from overlapping); the
     # per-kernel durations come from a profiled solve of the same batch
     params = lgk.default_params(precision=prec, device=local, profile=0, lo_refresh=int(refine),
-                                check_every=args.check_every)
+                                check_every=args.check_every, **knobs(args))
     from synth import cases as SC
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
@@ -398,7 +406,8 @@ def run_ours(args, rank, world, local):
     cs_p = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                            case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                            params=lgk.default_params(precision=prec, device=local, profile=1,
-                                                     lo_refresh=int(refine), check_every=args.check_every))
+                                                     lo_refresh=int(refine), check_every=args.check_every,
+                                                     **knobs(args)))
     if sw:
         pr = lgk.solve_stream(cs_p, W, None, width=sw, profile=True, **rule)["profile"]
         prof_iters = pr["gemm1"][1]          # iterations of the whole stream (one GEMM1 each)
@@ -424,7 +433,7 @@ def run_ours(args, rank, world, local):
                              case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                              params=lgk.default_params(precision=prec, device=local,
                                                        lo_refresh=int(refine),
-                                                       check_every=args.check_every))
+                                                       check_every=args.check_every, **knobs(args)))
         if sw:
             s2 = lgk.solve_stream(c2, W, None, width=sw, check=True, **rule)
             t, tau = s2["t"], s2["tau"]
@@ -498,6 +507,11 @@ def run_ours(args, rank, world, local):
             "two_pass": bench_two_pass(lgk, case, W, args, local)}
         if not args.no_k441 and args.workload == "cfg1":
             extra["k441"] = bench_k441(lgk, args, local)
+        if not args.no_serve and args.workload == "cfg1":
+            sv = serve_run(lgk, args, local, n_cases=24, rate=1.0, workers=2)
+            sv["note"] = ("a short stream of the serving workload (bench.py --serve N sweeps the "
+                          "arrival rate); latency = submit to results")
+            extra["serving"] = sv
         lat_ms = sorted(x * 1e3 for x in lat)
         out = {"metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
@@ -541,7 +555,7 @@ def bench_k441(lgk, args, local, width=128, steps=2, fp32_max_iter=4000):
     prec = PRECISIONS[args.precision]
     refine = args.precision == "bf16x3" and not args.exact
     params = lgk.default_params(precision=prec, device=local, lo_refresh=int(refine),
-                                check_every=args.check_every)
+                                check_every=args.check_every, **knobs(args))
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
                          case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, params=params)
     rule = dict(w0_bot=SC.W0_BOT, rho0=RHO0_PER_BETA * cs.beta, tol=args.tol, max_iter=args.max_iter)
@@ -665,7 +679,7 @@ def bench_two_pass(lgk, case, W, args, local, reps=2, n_ld=1000, delta=(1.0, 0.5
     pts, label, _ = SC.eval_grid(case, spacing=2.0, margin=25.0)
     phi_cand = SC.dose_rate(pts[label < 0], case.iso)
     params = lgk.default_params(precision=PRECISIONS[args.precision], device=local,
-                                lo_refresh=int(not args.exact))
+                                lo_refresh=int(not args.exact), **knobs(args))
     kw = dict(phi_cand=phi_cand, delta_ld1=delta[0], delta_ld2=delta[1], n_ld1=n_ld, n_ld2=n_ld,
               seed=seed, w0_bot=SC.W0_BOT, rho0_per_beta=RHO0_PER_BETA, tol=args.tol,
               max_iter=args.max_iter, params=params)
@@ -714,7 +728,8 @@ def serve_cases(n_req, seed=4000):
     """Serving workload: sizes log-uniform between the 8 mm sphere case
     (20 isocenters, 4500 points) and the 52 cm^3 ellipsoid case (150
     isocenters, 40000 points), 1 + floor(8u) targets, 81 or 441 weightings
-    (p = 1/2)."""
+    (p = 1/2); half of the cases get a follow-up request of 9 weightings (a
+    3 x 3 slider refinement around the grid's centre) for the same case."""
     from synth import cases as SC
     rng = np.random.default_rng(seed)
     out = []
@@ -733,12 +748,108 @@ def serve_cases(n_req, seed=4000):
                             n_ld2=rest - 2 * (rest // 3), n_iso=n_iso, seed=seed + 1 + r,
                             name=f"req{r}")
         grid = 9 if rng.uniform() < 0.5 else 21
-        out.append((case, SC.slider_weights(grid)))
+        follow = None
+        if rng.uniform() < 0.5:
+            s = np.array([0.4, 0.5, 0.6])
+            follow = np.array([(1.0, 1.0, a, SC.W0_BOT * 10.0 ** (3.0 * c)) for a in s for c in s])
+        out.append((case, SC.slider_weights(grid), follow))
     return out
 
 
-def run_serve(args, rank, world, local):
+def serve_run(lgk, args, local, n_cases, rate, workers, width=32, seed=4000):
+    """One Poisson stream of serving requests through lgk_server (continuous
+    batching): every case is opened as a resident case with its initial
+    request; a follow-up request for the same case arrives later in the
+    stream and joins the case's running stream (or finds it resident and
+    idle); a case is closed after its last request is submitted.  Returns
+    throughput and latency figures."""
     import threading
+    from synth import cases as SC
+    reqs = serve_cases(n_cases + 3, seed=seed)
+    warm, reqs = reqs[:3], reqs[3:]
+    srv = lgk.Server(workers=workers, tol=args.tol, max_iter=args.max_iter, w0_bot=SC.W0_BOT,
+                     rho0_per_beta=RHO0_PER_BETA, stream_width=width,
+                     params=lgk.default_params(device=local, **knobs(args)))
+
+    def open_case(case):
+        return srv.open(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                        case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal)
+
+    # capacity from three cases served one at a time (untimed)
+    service = []
+    for case, W, _ in warm:
+        t0 = time.perf_counter()
+        cid = open_case(case)
+        rid = srv.submit_to(cid, W)
+        srv.close_case(cid)
+        srv.wait(rid, case.n_iso, W.shape[0])
+        service.append(time.perf_counter() - t0)
+    cap = workers / float(np.mean(service))          # cases per second
+    lam = rate * cap
+    rng = np.random.default_rng(77)
+    t_case = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
+    events = []                                      # (time, kind, case index)
+    for k, (case, W, follow) in enumerate(reqs):
+        events.append((t_case[k], 0, k))
+        if follow is not None:
+            events.append((t_case[k] + rng.exponential(2.0 / lam), 1, k))
+    events.sort()
+    last = {}
+    for e in events:
+        last[e[2]] = e
+    ids = []                                         # (request id, n_iso, K, kind)
+    lock = threading.Lock()
+    results = []
+    cids = {}
+    submitted = threading.Semaphore(0)
+
+    def collector(n):
+        for _ in range(n):
+            submitted.acquire()
+            with lock:
+                rid, n_iso, K, kind = ids[len(results)]
+            info = srv.wait(rid, n_iso, K)[0]
+            with lock:
+                results.append((kind, info))
+
+    th = threading.Thread(target=collector, args=(len(events),))
+    th.start()
+    t0 = time.perf_counter()
+    for ev in events:
+        t_ev, kind, k = ev
+        delay = t0 + t_ev - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        case, W, follow = reqs[k]
+        if kind == 0:
+            cids[k] = open_case(case)
+        Wk = W if kind == 0 else follow
+        rid = srv.submit_to(cids[k], Wk)
+        if last[k] is ev:
+            srv.close_case(cids[k])
+        with lock:
+            ids.append((rid, case.n_iso, Wk.shape[0], kind))
+        submitted.release()
+    th.join()
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([i["total_ms"] for _, i in results])
+    lat_f = np.array([i["total_ms"] for kd, i in results if kd == 1])
+    conv = sum(i["converged"] for _, i in results)
+    n_plans = sum(i["K"] for _, i in results)
+    return {"value": conv / makespan, "unit": "plans/s", "cases": len(reqs),
+            "requests": len(results), "follow_ups": int(len(lat_f)), "workers": workers,
+            "stream_width": width, "arrival_rate_cases_per_s": lam, "rate_vs_capacity": rate,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "follow_up_p50": float(np.percentile(lat_f, 50)) if len(lat_f) else None,
+                           "follow_up_p99": float(np.percentile(lat_f, 99)) if len(lat_f) else None,
+                           "mean_queue": float(np.mean([i["queue_ms"] for _, i in results])),
+                           "mean_setup": float(np.mean([i["setup_ms"] for _, i in results]))},
+            "all_ok": all(i["status"] == 0 for _, i in results),
+            "converged_fraction": conv / n_plans, "makespan_s": makespan}
+
+
+def run_serve(args, rank, world, local):
     import torch
     from paper_2509_08602_b300 import build
     if rank == 0:
@@ -746,62 +857,15 @@ def run_serve(args, rank, world, local):
     barrier(world)
     torch.cuda.set_device(local)
     from paper_2509_08602_b300 import lgk
-    from synth import cases as SC
-    reqs = serve_cases(args.serve + 3)
-    warm, reqs = reqs[:3], reqs[3:]
-    srv = lgk.Server(workers=args.serve_workers, tol=args.tol, max_iter=args.max_iter,
-                     w0_bot=SC.W0_BOT, rho0_per_beta=RHO0_PER_BETA,
-                     params=lgk.default_params(device=local))
-
-    def submit(case, W):
-        return srv.submit(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
-                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, W)
-
-    # capacity estimate from three requests served one at a time (untimed)
-    service = []
-    for case, W in warm:
-        info, _, _ = srv.wait(submit(case, W), case.n_iso, W.shape[0])
-        service.append(info["total_ms"] / 1e3)
-    cap = args.serve_workers / float(np.mean(service))
-    lam = args.serve_rate * cap
-    rng = np.random.default_rng(77)
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(reqs)))
-    results = [None] * len(reqs)
-    ids = [None] * len(reqs)
-    ready = [threading.Event() for _ in reqs]
-
-    def collector():
-        for k, (case, W) in enumerate(reqs):
-            ready[k].wait()
-            results[k] = srv.wait(ids[k], case.n_iso, W.shape[0])[0]
-
-    th = threading.Thread(target=collector)
-    th.start()
-    t0 = time.perf_counter()
-    for k, (case, W) in enumerate(reqs):
-        delay = t0 + arrivals[k] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        ids[k] = submit(case, W)
-        ready[k].set()
-    th.join()
-    makespan = time.perf_counter() - t0
-    srv.close()
-    lat = np.array([r["total_ms"] for r in results])
-    conv = sum(r["converged"] for r in results)
-    line = {"metric": "served converged plans/s; p50/p99 request latency", "value": conv / makespan,
-            "unit": "plans/s", "n_gpus": world, "requests": len(reqs),
-            "workers": args.serve_workers, "arrival_rate_per_s": lam,
-            "rate_vs_capacity": args.serve_rate,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "mean_queue": float(np.mean([r["queue_ms"] for r in results])),
-                           "mean_setup": float(np.mean([r["setup_ms"] for r in results])),
-                           "mean_solve": float(np.mean([r["solve_ms"] for r in results]))},
-            "all_ok": all(r["status"] == 0 for r in results),
-            "converged_fraction": conv / sum(W.shape[0] for _, W in reqs),
-            "data": "synthetic", "dtype": "bf16",
-            "config": {"workload": "Poisson stream; sizes log-uniform 500x4660 .. 3750x41200, "
-                                   "1-8 targets, 81 or 441 weightings", "tol": args.tol}}
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    sweep = [serve_run(lgk, args, local, args.serve, r, args.serve_workers) for r in rates]
+    line = {"metric": "served converged plans/s; p50/p99 request latency",
+            "value": max(x["value"] for x in sweep), "unit": "plans/s", "n_gpus": world,
+            "sweep": sweep, "data": "synthetic", "dtype": "bf16",
+            "config": {"workload": f"Poisson stream of {args.serve} cases (sizes log-uniform 500x4660 .. "
+                                   "3750x41200, 1-8 targets, 81 or 441 weightings; half get a 9-weighting "
+                                   "follow-up request for the same resident case)", "tol": args.tol,
+                       "rates_vs_capacity": rates}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -829,13 +893,21 @@ def main():
                     help="BF16 form of A: bf16x3 (two BF16 terms; the plans match FP64), bf16 (one term)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the device plan-metrics and two-pass measurements")
+    ap.add_argument("--solve-refine", type=int, default=0,
+                    help="refinement steps of the solve per iteration (lgk_params.solve_refine)")
+    ap.add_argument("--setup-fp64", action="store_true",
+                    help="form S = A A^T + I with FP64 products instead of the tensor cores")
+    ap.add_argument("--rho-adapt", action="store_true",
+                    help="per-column residual balancing of rho (lgk_params.rho_adapt)")
     ap.add_argument("--no-k441", action="store_true",
                     help="skip the 441-weighting (5000 x 61600) measurement of the cfg1 line")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving mode: number of requests of a Poisson stream")
     ap.add_argument("--serve-workers", type=int, default=2)
-    ap.add_argument("--serve-rate", type=float, default=1.0,
-                    help="arrival rate as a multiple of the measured capacity")
+    ap.add_argument("--serve-rates", default="0.25,0.5,1,2",
+                    help="arrival rates to sweep, as multiples of the measured capacity")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the short serving run of the cfg1 line")
     args = ap.parse_args()
     rank, world, local = dist_init()
     if args.impl == "reference":

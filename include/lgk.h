@@ -122,6 +122,21 @@ typedef struct {
                                 (the multipliers rho y are unchanged).  The stop test and
                                 the reported plans use the column's current rho.
                                 0 (default): rho fixed per column (Eq. rho_rule or caller's). */
+    int solve_refine;        /* BF16 forms: iterative refinement steps of the x-update's solve
+                                per iteration, 0..2 (default 0).  v = S^{-1} rhs is a product
+                                with the explicit inverse whose FP32 sums lose accuracy when
+                                rhs is large along the directions S magnifies (v is then
+                                ~1000x smaller than rhs); each step computes the residual
+                                e = rhs - S v (with S kept as three BF16 terms, 6 products)
+                                and adds S^{-1} e, so A x1 - x2 = rhs - S v (Sec. 2.B) is
+                                held to the product's accuracy instead.  Each step costs two
+                                solve-sized products; S takes 6 m^2 more device bytes.      */
+    int setup_fp64;          /* BF16 forms: 1 forms S = A A^T + I with FP64 products on the CUDA
+                                cores (exact from the rounded A; slow on this GPU's FP64 rate);
+                                0 (default): on the tensor cores from A's BF16 terms (exact
+                                products, FP32 sums over 128 columns of A, FP64 sums of those;
+                                about 1e-6 relative error per entry).  The FP32 form always
+                                uses FP64 products.                                          */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
@@ -470,10 +485,12 @@ int lgk_fetch_state(const lgk_result* res, double* q1, double* q2);
  * BF16 forms run the q1 update inside the tensor-core GEMM2's epilogue
  * (LGK_K_Q1_UPDATE reports zero launches for them); the FP32 form launches
  * it.  GEMM1_LO / GEMM2_LO (lo R1 and lo^T v) run on the full iterations of
- * LGK_PREC_BF16X3 with lo_refresh = 1. */
+ * LGK_PREC_BF16X3 with lo_refresh = 1.  With solve_refine > 0 each refinement
+ * step adds SV (S v), REDUCE_ERR (e = rhs - S v), SOLVE and REDUCE_SOLVE after
+ * the first REDUCE_SOLVE. */
 enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLVE = 3,
        LGK_K_GEMM2 = 4, LGK_K_Q1_UPDATE = 5, LGK_K_FINALIZE = 6, LGK_K_GEMM1_LO = 7,
-       LGK_K_GEMM2_LO = 8, LGK_K_COUNT = 9 };
+       LGK_K_GEMM2_LO = 8, LGK_K_SV = 9, LGK_K_REDUCE_ERR = 10, LGK_K_COUNT = 11 };
 
 /* Per-kernel-class device time of a solve made with lgk_params.profile = 1:
  * ms[LGK_K_COUNT] total milliseconds between CUDA events recorded on the
@@ -483,51 +500,78 @@ enum { LGK_K_GEMM1 = 0, LGK_K_REDUCE_RHS = 1, LGK_K_SOLVE = 2, LGK_K_REDUCE_SOLV
 int lgk_fetch_profile(const lgk_result* res, double* ms, long long* launches);
 
 /* ------------------------------------------------------------------ serving
- * A request loop for planning requests (a case plus its K weightings) that
- * arrive over time.  Each admitted request runs lgk_create_case,
- * lgk_solve_weightings and lgk_fetch_times on a worker thread with its own
- * CUDA stream, so requests that arrive while others are on the GPU run
- * alongside them.  Admission is first come, first served under a device-
- * memory budget: a request starts once its estimated peak footprint (set-up
- * temporaries included) fits next to the requests in flight; one that can
- * never fit fails with LGK_EBUDGET.  A request's results do not depend on
- * what runs beside it (bitwise: every reduction has a fixed order).
- * (The paper plans one case at a time; this is the serving form of the
- * library, not a step of the method.)
+ * A request loop with continuous batching for planning requests that arrive
+ * over time.  (The paper plans one case at a time; this is the serving form
+ * of the library, not a step of the method.)
+ *
+ * A resident case is a case kept on the device (A, S^{-1} and the ADMM state
+ * of its columns).  Cases are admitted first come, first served under a
+ * device-memory budget: a case is set up once its estimated peak footprint
+ * (set-up temporaries included) fits next to the cases in flight; one that
+ * can never fit fails with LGK_EBUDGET.  Each admitted case runs on a worker
+ * thread with its own CUDA stream as one streaming solve of `stream_width`
+ * columns (lgk_solve_stream's iteration): every weighting submitted for the
+ * case, by any request and at any time while it is resident, takes the next
+ * column that frees up (at the next replay boundary, every 5 residual-test
+ * intervals).  Requests that arrive while the case is on the GPU thus join
+ * its running batch, and cases on different workers overlap on the device.
+ * A weighting's result does not depend on what runs beside it or when it
+ * entered (bitwise: columns never interact, every column starts alike, and
+ * every reduction has a fixed order).
+ * Per-weighting stop test, tolerance and iteration cap: those of
+ * lgk_solve_stream with the server's tol and max_iter, rho by Eq. rho_rule.
+ * A case that is continuously busy for 2^30 iterations of its stream (about
+ * 60 hours at 200 us per iteration) fails its requests with LGK_EINVAL.
  */
 typedef struct lgk_server lgk_server;
 
 typedef struct {
     lgk_params case_params;  /* per-case parameters (its stream field is ignored)           */
-    size_t hbm_budget;       /* bytes for the requests in flight; 0 = 90 % of free memory   */
-    int workers;             /* requests in flight at most (>= 1)                           */
-    double tol;              /* stop tolerance of every solve (lgk_solve_weightings)        */
-    int max_iter;
+    size_t hbm_budget;       /* bytes for the cases in flight; 0 = 90 % of free memory      */
+    int workers;             /* resident cases on the device at once (>= 1)                 */
+    double tol;              /* stop tolerance of every weighting                            */
+    int max_iter;            /* iteration cap of every weighting                             */
     double w0_bot;           /* rho rule: rho = rho0_per_beta * beta * sqrt(w0_bot / w_BOT) */
     double rho0_per_beta;
+    int stream_width;        /* columns of each case's streaming solve; 0 = 32              */
 } lgk_server_params;
 
 typedef struct {
     int status;              /* lgk_status of the request                                   */
     int K, n_iso;
-    double queue_ms;         /* submit -> admitted                                           */
-    double setup_ms;         /* lgk_create_case                                              */
-    double solve_ms;         /* lgk_solve_weightings + lgk_fetch_times                       */
+    double queue_ms;         /* submit -> its first weighting takes a column                 */
+    double setup_ms;         /* the case's set-up, if the request waited for it; else 0      */
+    double solve_ms;         /* first weighting in a column -> last weighting done           */
     double total_ms;         /* submit -> done                                               */
     int max_iters;           /* iterations of the slowest weighting                          */
     int converged;           /* weightings that met the tolerance                            */
-    size_t footprint;        /* estimated peak device bytes used for admission               */
+    size_t footprint;        /* estimated peak device bytes of the case (admission)          */
 } lgk_request_info;
 
 int lgk_server_create(const lgk_server_params* p, lgk_server** out);
-/* Copies the case arrays and W (K x 4); *id receives the request id. */
+/* One-shot request: a new resident case (desc copied) with the K weightings
+ * W (K x 4, copied; w_BOT > 0); the case leaves the device once they are
+ * done.  *id receives the request id. */
 int lgk_server_submit(lgk_server* s, const lgk_case_desc* desc, int K, const double* W,
                       long long* id);
+/* Queue a resident case (desc copied) for admission; *case_id receives its id.
+ * It stays resident, taking weightings from lgk_server_submit_to, until
+ * lgk_server_close.  LGK_EBUDGET if it can never fit the budget. */
+int lgk_server_open(lgk_server* s, const lgk_case_desc* desc, long long* case_id);
+/* A request of K weightings (W: K x 4, copied; w_BOT > 0) for resident case
+ * case_id: they join its running stream as columns free up.  *id receives
+ * the request id.  LGK_EINVAL if the case is unknown or closed. */
+int lgk_server_submit_to(lgk_server* s, long long case_id, int K, const double* W, long long* id);
+/* No more requests for case_id: it leaves the device once its queued
+ * weightings are done. */
+int lgk_server_close(lgk_server* s, long long case_id);
 /* Waits (at most timeout_ms) for request id; fills *info and, if not NULL,
- * t (K x 24N) and tau (K x N).  A request can be waited for once. */
+ * t (K x 24N) and tau (K x N) in the request's weighting order.  A request
+ * can be waited for once. */
 int lgk_server_wait(lgk_server* s, long long id, int timeout_ms, lgk_request_info* info,
                     double* t, double* tau);
-/* Finishes the requests in flight, drops queued ones, joins the workers. */
+/* Finishes the weightings in the cases' columns, fails the queued ones
+ * (LGK_ETIMEOUT, "server destroyed"), joins the workers. */
 void lgk_server_destroy(lgk_server* s);
 
 void lgk_free_result(lgk_result* res);

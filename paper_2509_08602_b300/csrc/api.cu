@@ -78,6 +78,8 @@ int lgk_default_params(lgk_params* p) {
     p->lo_refresh = 1;
     p->lo_refresh_iters = 8000;
     p->rho_adapt = 0;
+    p->solve_refine = 0;
+    p->setup_fp64 = 0;
     return LGK_OK;
 }
 
@@ -91,6 +93,8 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     if (prm.lo_refresh != 0 && prm.lo_refresh != 1) return fail(LGK_EINVAL, "lo_refresh must be 0 or 1");
     if (prm.lo_refresh_iters < 0) return fail(LGK_EINVAL, "lo_refresh_iters must be >= 0");
     if (prm.rho_adapt != 0 && prm.rho_adapt != 1) return fail(LGK_EINVAL, "rho_adapt must be 0 or 1");
+    if (prm.solve_refine < 0 || prm.solve_refine > 2) return fail(LGK_EINVAL, "solve_refine must be 0, 1 or 2");
+    if (prm.setup_fp64 != 0 && prm.setup_fp64 != 1) return fail(LGK_EINVAL, "setup_fp64 must be 0 or 1");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

@@ -161,7 +161,7 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
 // parts (the solve amplifies input rounding).  Four rows per thread; grid
 // (m_pad / 256, Kp), 64 threads.
 template <bool BF16>
-__global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs) {
+__global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs, float* rhs32) {
     pdl_trigger();
     pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
@@ -190,24 +190,75 @@ __global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void*
         *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(hi);
         *reinterpret_cast<uint2*>(d + plane) = *reinterpret_cast<const uint2*>(mid);
         *reinterpret_cast<uint2*>(d + 2 * plane) = *reinterpret_cast<const uint2*>(lo);
+        if (rhs32) *reinterpret_cast<float4*>(rhs32 + o) = make_float4(r[0], r[1], r[2], r[3]);
     } else {
         *reinterpret_cast<float4*>(static_cast<float*>(rhs) + o) = make_float4(r[0], r[1], r[2], r[3]);
     }
 }
 
+__device__ inline void split3_store(const float v[4], __nv_bfloat16* d, size_t plane) {
+    __nv_bfloat16 hi[4], mid[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        hi[k] = __float2bfloat16_rn(v[k]);
+        const float r1 = v[k] - __bfloat162float(hi[k]);
+        mid[k] = __float2bfloat16_rn(r1);
+        lo[k] = __float2bfloat16_rn(r1 - __bfloat162float(mid[k]));
+    }
+    *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(hi);
+    *reinterpret_cast<uint2*>(d + plane) = *reinterpret_cast<const uint2*>(mid);
+    *reinterpret_cast<uint2*>(d + 2 * plane) = *reinterpret_cast<const uint2*>(lo);
+}
+
+// Refinement of the solve (lgk_params.solve_refine): e = rhs - S v, with
+// rhs kept in FP32 by k_reduce_rhs and S v summed from the S . V3 product's
+// stream-K slots; e goes into the solve's input planes (three BF16 terms) for
+// the next product with S^{-1}.  Grid (m_pad / 256, Kp), 64 threads.
+__global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const float* __restrict__ rhs32,
+                                                   __nv_bfloat16* rhs) {
+    pdl_trigger();
+    pdl_wait();
+    if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
+    const int i = blockIdx.x * 256 + threadIdx.x * 4, j = blockIdx.y;
+    const size_t o = (size_t)j * cx.m_pad + i;
+    const float4 sv = gemm_out4(src, i, j);
+    const float4 b = *reinterpret_cast<const float4*>(rhs32 + o);
+    const float e[4] = {b.x - sv.x, b.y - sv.y, b.z - sv.z, b.w - sv.w};
+    split3_store(e, rhs + o, (size_t)cx.Kp * cx.m_pad);
+}
+
 // v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block (one
 // per 128-row tile and column: one warp per 128 rows, four rows per thread).
 // Grid (m_pad / 256, Kp), 64 threads.
-template <bool BF16>
-__global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, void* V) {
+// MODE (solve refinement, lgk_params.solve_refine):
+//   RS_PLAIN  v = S^{-1} rhs from the slots; the q2 step below
+//   RS_FIRST  v0 = the slots: kept in FP32 (rv) and as three BF16 terms (V3)
+//             for the refinement's S v0; no state update yet
+//   RS_ACCUM  v = rv + the slots (a correction S^{-1} e), kept as RS_FIRST
+//   RS_FINAL  v = rv + the slots; the q2 step below
+enum { RS_PLAIN = 0, RS_FIRST = 1, RS_FINAL = 2, RS_ACCUM = 3 };
+
+template <bool BF16, int MODE>
+__global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, void* V, float* rv,
+                                                     __nv_bfloat16* V3) {
     pdl_trigger();
     pdl_wait();
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.y;
     const int rt = blockIdx.x * 2 + w, i = rt * 128 + lane * 4;
-    const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
     const size_t o = (size_t)j * cx.m_pad + i;
-    const float4 v = gemm_out4(src, i, j);
+    float4 v = gemm_out4(src, i, j);
+    if (MODE == RS_ACCUM || MODE == RS_FINAL) {
+        const float4 p = *reinterpret_cast<const float4*>(rv + o);
+        v = make_float4(p.x + v.x, p.y + v.y, p.z + v.z, p.w + v.w);
+    }
+    if (MODE == RS_FIRST || MODE == RS_ACCUM) {
+        *reinterpret_cast<float4*>(rv + o) = v;
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+        split3_store(vv, V3 + o, (size_t)cx.Kp * cx.m_pad);
+        return;
+    }
+    const bool check = is_check_iter(cx.ctrl, cx.check_every, cx.tol);
     const float4 qo = *reinterpret_cast<const float4*>(cx.q2 + o);
     float qn[4], res[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -516,7 +567,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     count_launch();
     prof_mark(r, itx, 1);
     dim3 gm(cs.m_pad / 256, r.Kp);
-    k_reduce_rhs<false><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p);
+    k_reduce_rhs<false><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.rhs.p, nullptr);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 2);
     // solve: part = rhs . G^T (G symmetric)
@@ -528,7 +579,7 @@ static int iteration_fp32(ResultData& r, const IterCtx& cx, int itx) {
     }
     count_launch();
     prof_mark(r, itx, 3);
-    k_reduce_solve<false><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p);
+    k_reduce_solve<false, RS_PLAIN><<<gm, 64, 0, st>>>(cx, plain_src(part, cs.m_pad), r.V.p, nullptr, nullptr);
     LGK_LAUNCH_CHECK();
     prof_mark(r, itx, 4);
     // GEMM2: W[Kp][n_pad] = V[Kp][m_pad] . A[m_pad][n_pad]
@@ -568,31 +619,62 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     const bool test_slot = (itx + 1) % cs.prm.check_every == 0;
     const bool full = r.refine && (itx == 0 || test_slot);
     const bool first_only = itx == 0 && !test_slot;
-    auto ran = [&](int k, bool v) {
+    int k = 0;                       // launch slot of this iteration (profile events)
+    auto ran = [&](bool v) {
         if (!r.prof_ran.empty()) r.prof_ran[(size_t)itx * r.prof_class.size() + k] = v;
     };
+    auto next = [&]() { prof_mark(r, itx, ++k); };
     prof_mark(r, itx, 0);
     if (full && (rc = tc_gemm1_lo(r, pdl && itx > 0, first_only))) return rc;
-    ran(0, full);
-    prof_mark(r, itx, 1);
+    ran(full);
+    next();
     if ((rc = tc_gemm1(r, pdl && (itx > 0 || full)))) return rc;
-    prof_mark(r, itx, 2);
-    LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p));
+    next();
+    float* rhs32 = r.refine_steps ? r.rhs32.as<float>() : nullptr;
+    __nv_bfloat16* V3 = r.refine_steps ? r.V3.as<__nv_bfloat16>() : nullptr;
+    float* rv = r.refine_steps ? r.rv.as<float>() : nullptr;
+    LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan1), r.rhs.p, rhs32));
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 3);
+    next();
     if ((rc = tc_solve(r, pdl))) return rc;
-    prof_mark(r, itx, 4);
-    LGK_CUDA_TRY(launch_k(k_reduce_solve<true>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan_s), r.V.p));
+    next();
+    if (r.refine_steps == 0) {
+        LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_PLAIN>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan_s),
+                              r.V.p, rv, V3));
+    } else {
+        LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FIRST>, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan_s),
+                              r.V.p, rv, V3));
+    }
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 5);
+    next();
+    // refinement: e = rhs - S v, v += S^{-1} e
+    for (int step = 1; step <= r.refine_steps; ++step) {
+        if ((rc = tc_sv(r, pdl))) return rc;
+        next();
+        LGK_CUDA_TRY(launch_k(k_reduce_err, gm, dim3(64), 0, st, pdl, cx, plan_src(r, r.plan_s), rhs32,
+                              r.rhs.as<__nv_bfloat16>()));
+        LGK_LAUNCH_CHECK();
+        next();
+        if ((rc = tc_solve(r, pdl))) return rc;
+        next();
+        if (step < r.refine_steps) {
+            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_ACCUM>, gm, dim3(64), 0, st, pdl, cx,
+                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
+        } else {
+            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FINAL>, gm, dim3(64), 0, st, pdl, cx,
+                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
+        }
+        LGK_LAUNCH_CHECK();
+        next();
+    }
     if (full && (rc = tc_gemm2_lo(r, pdl, first_only))) return rc;
-    ran(5, full);
-    prof_mark(r, itx, 6);
+    ran(full);
+    next();
     if ((rc = tc_gemm2(r, pdl))) return rc;
-    prof_mark(r, itx, 7);
+    next();
     LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
     LGK_LAUNCH_CHECK();
-    prof_mark(r, itx, 8);
+    next();
     return LGK_OK;
 }
 
@@ -671,6 +753,10 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if (!bf16 && (rc = r.part.alloc(mq * 4))) return rc;     // BF16 forms: tc_prepare
     if ((rc = r.utab.alloc(utab.size() * 4)) || (rc = r.colp.alloc(colp.size() * 4))) return rc;
     r.refine = cs.na == 2 && cs.prm.lo_refresh;
+    r.refine_steps = bf16 && cs.S3.p ? cs.prm.solve_refine : 0;
+    if (r.refine_steps) {
+        if ((rc = r.rhs32.alloc(mq * 4)) || (rc = r.rv.alloc(mq * 4)) || (rc = r.V3.alloc(mq * 6))) return rc;
+    }
     if (r.refine) {
         if ((rc = r.c1.alloc(mq * 4)) || (rc = r.c2.alloc(nq * 4))) return rc;
         LGK_CUDA_TRY(cudaMemsetAsync(r.c1.p, 0, r.c1.bytes, st));
@@ -683,21 +769,30 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.n_resid_m = cs.m_pad / 128;
     if ((rc = r.resid.alloc((size_t)(r.n_resid_n + r.n_resid_m) * Kp * 5 * 8))) return rc;
     if ((rc = r.stats.alloc((size_t)3 * Kp * 8))) return rc;
-    // streaming: the weighting each column holds (-1: none), the iteration
-    // it started at, the next weighting to admit
-    std::vector<int> w_of, start_it;
+    // iterations per captured graph (one replay)
+    const int per_graph = std::max(1, std::min(r.max_iter, 5 * cs.prm.check_every));
+    // streaming: the weighting (tag) each column holds (-1: none), the
+    // iteration it started at, the next weighting to admit.  A dynamic
+    // stream's counter starts at one replay, so no column gets the first-
+    // iteration refresh of the lagged products: every column, initial or
+    // refilled, runs the same iteration from its own start.
+    const bool dynamic = stream && stream->pull;
+    const int n0 = stream && stream->n_initial >= 0 ? std::min(stream->n_initial, K) : K;
+    const int iter0 = dynamic ? per_graph : 0;
+    std::vector<long long> tag_of;
+    std::vector<int> start_it;
     int next_w = K;
     DevBuf cols_d, lam_d;
     if (stream) {
-        w_of.assign(Kp, -1);
-        start_it.assign(Kp, 0);
-        for (int j = 0; j < K; ++j) w_of[j] = j;
+        tag_of.assign(Kp, -1);
+        start_it.assign(Kp, iter0);
+        for (int j = 0; j < n0; ++j) tag_of[j] = stream->initial_tags ? stream->initial_tags[j] : j;
         if ((rc = cols_d.alloc((size_t)Kp * 4)) || (rc = lam_d.alloc((size_t)Kp * cs.m * 8))) return rc;
     }
 
     std::vector<int> act(2 * Kp, 0);
-    for (int j = 0; j < K; ++j) act[j] = 1;
-    Control c0{0, K, r.max_iter, 0, 0};
+    for (int j = 0; j < n0; ++j) act[j] = 1;
+    Control c0{iter0, n0, r.max_iter, 0, 0};
     LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
     LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
     if (mask)
@@ -739,12 +834,15 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     }
 
     // capture a CUDA graph of `per_graph` iterations, replay until done
-    int per_graph = std::max(1, std::min(r.max_iter, 5 * cs.prm.check_every));
     cudaGraph_t g = nullptr;
     // kernel classes of one iteration, in launch order
-    if (bf16)
-        r.prof_class = {LGK_K_GEMM1_LO, LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
-                        LGK_K_GEMM2_LO, LGK_K_GEMM2, LGK_K_FINALIZE};
+    if (bf16) {
+        r.prof_class = {LGK_K_GEMM1_LO, LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE};
+        for (int step = 0; step < r.refine_steps; ++step)
+            r.prof_class.insert(r.prof_class.end(),
+                                {LGK_K_SV, LGK_K_REDUCE_ERR, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE});
+        r.prof_class.insert(r.prof_class.end(), {LGK_K_GEMM2_LO, LGK_K_GEMM2, LGK_K_FINALIZE});
+    }
     else
         r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
                         LGK_K_GEMM2, LGK_K_Q1_UPDATE, LGK_K_FINALIZE};
@@ -799,6 +897,40 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     // cap), give those columns the next weightings, and push the new flags,
     // tables and counters.  done: no column holds a weighting; age: the
     // iterations of the oldest running column.
+    // the next weighting of the stream: from the caller's arrays, or pulled
+    // from a dynamic source (1: one, 0: none now, -1: closed and drained)
+    auto next_weighting = [&](double* w, double* rh, long long* tag, bool block) -> int {
+        const StreamSpec& ss = *stream;
+        if (ss.pull) return ss.pull(w, rh, tag, block);
+        if (next_w >= ss.K_total) return -1;
+        std::copy(ss.W + 4 * (size_t)next_w, ss.W + 4 * (size_t)next_w + 4, w);
+        *rh = ss.rho[next_w];
+        *tag = next_w++;
+        return 1;
+    };
+    auto emit = [&](long long tag, const StreamOut& o) {
+        const StreamSpec& ss = *stream;
+        if (ss.done) {
+            ss.done(tag, o);
+            return;
+        }
+        const size_t w = (size_t)tag;
+        if (ss.iters) ss.iters[w] = o.iters;
+        if (ss.obj) ss.obj[w] = o.obj;
+        if (ss.rel_pri) ss.rel_pri[w] = o.rel_pri;
+        if (ss.rel_dual) ss.rel_dual[w] = o.rel_dual;
+        if (ss.converged) ss.converged[w] = (uint8_t)o.converged;
+        if (ss.check && o.check) std::copy(o.check, o.check + LGK_CHECK_COUNT, ss.check + w * LGK_CHECK_COUNT);
+        if (ss.t) std::copy(o.t, o.t + cs.n_beams, ss.t + w * cs.n_beams);
+        if (ss.tau) std::copy(o.tau, o.tau + cs.n_iso, ss.tau + w * cs.n_iso);
+    };
+    // streaming, at a replay boundary (the device idle): copy out the results
+    // of the columns that stopped (their test passed, or their own iteration
+    // cap), give every free column the next weighting, and push the new
+    // flags, tables and counters.  A dynamic stream with no weighting left in
+    // any column waits here for the next one (its counter restarts).  done:
+    // no column holds a weighting and none will come; age: the iterations of
+    // the oldest running column.
     auto stream_boundary = [&](bool& done, int& age) -> int {
         const StreamSpec& ss = *stream;
         std::vector<int> a(2 * (size_t)Kp), its(Kp);
@@ -807,11 +939,13 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         LGK_CUDA_TRY(cudaStreamSynchronize(st));
         std::vector<int> ret;
         for (int j = 0; j < Kp; ++j) {
-            if (w_of[j] < 0) continue;
+            if (tag_of[j] < 0) continue;
             if (a[j] && hc->iter - start_it[j] >= ss.max_iter) a[j] = 0;
             if (!a[j]) ret.push_back(j);
         }
+        bool changed = false;
         if (!ret.empty()) {
+            changed = true;
             k_objective<<<Kp, 256, 0, st>>>(cx, r.stats.as<double>() + 2 * Kp);
             LGK_LAUNCH_CHECK();
             LGK_CUDA_TRY(cudaMemcpyAsync(cols_d.p, ret.data(), ret.size() * 4, cudaMemcpyHostToDevice, st));
@@ -823,39 +957,54 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             LGK_CUDA_TRY(cudaMemcpyAsync(lam.data(), lam_d.p, lam.size() * 8, cudaMemcpyDeviceToHost, st));
             LGK_CUDA_TRY(cudaStreamSynchronize(st));
             std::vector<double> chk;
-            if (ss.check) {     // FP64 check of the stopped columns, before they are refilled
+            if (ss.check || ss.want_check) {   // FP64 check of the stopped columns, before refilling
                 chk.resize(ret.size() * (size_t)LGK_CHECK_COUNT);
                 const int rcc = run_check(r, ret.data(), (int)ret.size(), chk.data());
                 if (rcc) return rcc;
             }
-            // graph slots assume replays that start on a multiple of their
-            // length; the counter stops early only once no column runs
-            hc->iter = (int)round_up(hc->iter, per_graph);
-            std::vector<int> fill;
             for (size_t c = 0; c < ret.size(); ++c) {
-                const int j = ret[c], w = w_of[j];
-                if (ss.iters) ss.iters[w] = its[j] - start_it[j];
-                if (ss.obj) ss.obj[w] = stv[2 * (size_t)Kp + j];
-                if (ss.rel_pri) ss.rel_pri[w] = stv[j];
-                if (ss.rel_dual) ss.rel_dual[w] = stv[(size_t)Kp + j];
-                if (ss.converged) ss.converged[w] = (uint8_t)(a[(size_t)Kp + j] != 0);
-                if (ss.check)
-                    std::copy(&chk[c * LGK_CHECK_COUNT], &chk[c * LGK_CHECK_COUNT] + LGK_CHECK_COUNT,
-                              ss.check + (size_t)w * LGK_CHECK_COUNT);
+                const int j = ret[c];
                 const double* l = &lam[c * (size_t)cs.m];
-                if (ss.t) std::copy(l, l + cs.n_beams, ss.t + (size_t)w * cs.n_beams);
-                if (ss.tau) std::copy(l + cs.n_beams, l + cs.m, ss.tau + (size_t)w * cs.n_iso);
-                w_of[j] = -1;
-                if (next_w < ss.K_total) {
-                    w_of[j] = next_w;
-                    start_it[j] = hc->iter;
-                    fill_col(j, ss.W + 4 * (size_t)next_w, ss.rho[next_w], cs.slot_count.data());
-                    a[j] = 1;
-                    a[(size_t)Kp + j] = 0;
-                    fill.push_back(j);
-                    ++next_w;
-                }
+                StreamOut o{l, l + cs.n_beams, its[j] - start_it[j], stv[2 * (size_t)Kp + j], stv[j],
+                            stv[(size_t)Kp + j], a[(size_t)Kp + j] != 0,
+                            chk.empty() ? nullptr : &chk[c * LGK_CHECK_COUNT]};
+                emit(tag_of[j], o);
+                tag_of[j] = -1;
             }
+        }
+        // give every free column the next weighting
+        std::vector<int> fill;
+        bool closed = false;
+        auto take = [&](int j, bool block) -> bool {
+            double w[4], rh;
+            long long tag;
+            const int got = next_weighting(w, &rh, &tag, block);
+            if (got < 0) closed = true;
+            if (got != 1) return false;
+            tag_of[j] = tag;
+            fill_col(j, w, rh, cs.slot_count.data());
+            a[j] = 1;
+            a[(size_t)Kp + j] = 0;
+            fill.push_back(j);
+            return true;
+        };
+        // (the stream's width is K columns; the padding columns up to Kp stay empty)
+        for (int j = 0; j < K && !closed; ++j)
+            if (tag_of[j] < 0 && !take(j, false)) break;
+        bool any = false;
+        for (int j = 0; j < Kp; ++j) any = any || tag_of[j] >= 0;
+        if (!any && dynamic && !closed) {
+            // idle: wait for the next weighting; the counter restarts at one replay
+            hc->iter = iter0;
+            if (take(0, true))
+                for (int j = 1; j < K && !closed; ++j)
+                    if (!take(j, false)) break;
+            changed = true;
+        }
+        if (changed) {
+            // graph slots assume replays that start on a multiple of their length
+            hc->iter = (int)round_up(hc->iter, per_graph);
+            for (int j : fill) start_it[j] = hc->iter;
             if (!fill.empty()) {
                 LGK_CUDA_TRY(cudaMemcpyAsync(r.utab.p, utab.data(), utab.size() * 4, cudaMemcpyHostToDevice, st));
                 LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.p, colp.data(), colp.size() * 4, cudaMemcpyHostToDevice, st));
@@ -878,7 +1027,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         done = true;
         age = 0;
         for (int j = 0; j < Kp; ++j)
-            if (w_of[j] >= 0) {
+            if (tag_of[j] >= 0) {
                 done = false;
                 age = std::max(age, hc->iter - start_it[j]);
             }
@@ -939,6 +1088,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     auto t0 = std::chrono::steady_clock::now();
     rc = LGK_OK;
     for (;;) {
+        if (dynamic) t0 = std::chrono::steady_clock::now();     // a server stream: bound each replay
         cudaError_t le = cudaGraphLaunch(r.graph, st);
         if (le != cudaSuccess) { set_error(cudaGetErrorString(le)); rc = LGK_ECUDA; break; }
         count_launch((long long)n_nodes - 0);

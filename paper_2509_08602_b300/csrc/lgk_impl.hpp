@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <condition_variable>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -52,6 +53,7 @@ struct CaseData {
     int na = 0;        // BF16 terms of A: 1 (LGK_PREC_BF16), 2 (LGK_PREC_BF16X3)
     DevBuf G32;        // float [m_pad][m_pad] S^{-1}    (LGK_PREC_FP32)
     DevBuf G3;         // bf16 [3][m_pad][m_pad] S^{-1} = hi + mid + lo (BF16 forms)
+    DevBuf S3;         // bf16 [3][m_pad][m_pad] S = hi + mid + lo (BF16 forms, solve_refine > 0)
     DevBuf ctrl_setup; // int [4] device error flags during set-up
     std::atomic<int> async_busy{0};   // an asynchronous solve of this case is running
     size_t bytes_held() const;
@@ -65,6 +67,7 @@ struct TcMaps {
     CUtensorMap G3;     // S^{-1} hi/mid/lo, 128 x 64 tiles (solve)
     CUtensorMap R1, rhs, V;   // hi/lo iterates, n_tile x 64 tiles
     CUtensorMap Alo_k, Alo_mn;   // A's low BF16 term alone (lo_refresh products)
+    CUtensorMap S3, V3;          // S hi/mid/lo (128 x 64 tiles) and v's three terms (refinement)
 };
 
 // Stream-K work plan of one tensor-core GEMM (device int arrays, see
@@ -99,6 +102,8 @@ struct ResultData {
     bool refine = false;      // lo_refresh: heavy products with A_hi, lo products lagged
     bool wide = false;        // GEMM1 / GEMM2 (and the lo products) on 256-row tiles
     DevBuf c1, c2;            // float [Kp][m_pad] lo R1_hi, [Kp][n_pad] lo^T V_hi (last full iteration)
+    int refine_steps = 0;     // solve refinement steps per iteration (lgk_params.solve_refine)
+    DevBuf rhs32, rv, V3;     // refinement: rhs FP32 [Kp][m_pad], v so far FP32, v as bf16 [3][Kp][m_pad]
     DevBuf mask;              // uint32 [n_pad][mask_words] point selection, when given
     int mask_words = 0;       // 0: every point in every column
     DevBuf colp;              // float [4][Kp]: rho, 1/rho, w_BOT, unused
@@ -135,9 +140,20 @@ struct ResultData {
 // set-up (setup.cu)
 int setup_case(CaseData& cs, const lgk_case_desc& d);
 
+// Result of one weighting of a stream (host memory, valid during the call).
+struct StreamOut {
+    const double* t;         // n_beams sector times (unscaled)
+    const double* tau;       // n_iso isocenter times
+    int iters;
+    double obj, rel_pri, rel_dual;
+    bool converged;
+    const double* check;     // LGK_CHECK_COUNT values of the FP64 check, or null
+};
+
 // Streaming solve (lgk_solve_stream): K_total weightings admitted into the
 // columns of one solve as earlier ones stop; results are written per
-// weighting (host arrays, each may be null).
+// weighting (host arrays, each may be null).  With `pull` set (serving), the
+// weightings come from it instead of W / rho and the results go to `done`.
 struct StreamSpec {
     int K_total = 0;
     const double* W = nullptr;       // K_total x 4
@@ -147,6 +163,13 @@ struct StreamSpec {
     int* iters = nullptr;
     uint8_t* converged = nullptr;
     double* check = nullptr;         // K_total x LGK_CHECK_COUNT (FP64 check per weighting)
+    // dynamic source: pull(w[4], &rho, &tag, block) returns 1 (a weighting),
+    // 0 (none now; only when !block) or -1 (closed and drained)
+    std::function<int(double*, double*, long long*, bool)> pull;
+    std::function<void(long long, const StreamOut&)> done;
+    bool want_check = false;         // run the FP64 check for `done`
+    int n_initial = -1;              // columns filled at the start (run_solve's W rows); -1: all
+    const long long* initial_tags = nullptr;
 };
 
 // one solve (iter.cu); with `stream`, W and rho hold its first r.K weightings
@@ -170,6 +193,12 @@ int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
           const double* A, int lda, const double* B, int ldb, double beta,
           double* C, int ldc);
 
+// BF16 tensor map of `parts` stacked [rows][cols] matrices, box 64 x box_rows (tc_gemm.cu)
+int make_tma_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint64_t parts,
+                 uint32_t box_rows);
+// S = I + A A^T from the case's BF16 terms on the tensor cores (syrk.cu)
+int tc_syrk(CaseData& cs, double* S, int* err);
+
 // Tensor-core GEMMs (tc_gemm.cu)
 int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt);
 int sm_count();
@@ -182,6 +211,7 @@ int tc_gemm1(ResultData& r, bool pdl = false);     // part[s] = Ahat . R1^T over
 int tc_gemm1_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_gemm2_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_solve(ResultData& r, bool pdl = false);     // part[s] = G3 . rhs^T  (6 products)
+int tc_sv(ResultData& r, bool pdl = false);        // part[s] = S3 . V3^T   (6 products, refinement)
 int tc_gemm2(ResultData& r, bool pdl = false);     // fused: q1, R1 update from Ahat^T . V
 
 }  // namespace lgk

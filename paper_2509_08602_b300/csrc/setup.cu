@@ -27,7 +27,7 @@ int DevBuf::alloc(size_t n) {
 }
 
 size_t CaseData::bytes_held() const {
-    return col_slot.bytes + Dr.bytes + A32.bytes + Ahat.bytes + G32.bytes + G3.bytes +
+    return col_slot.bytes + Dr.bytes + A32.bytes + Ahat.bytes + G32.bytes + G3.bytes + S3.bytes +
            cublas_ws.bytes + ctrl_setup.bytes;
 }
 
@@ -320,6 +320,24 @@ __global__ void k_inverse_out(const double* G, size_t total, float* g32, __nv_bf
     }
 }
 
+// S (lower triangle computed, FP64) -> three BF16 terms of the full symmetric
+// matrix, hi + mid + lo, for the solve's refinement (S v in the residual).
+__global__ void k_split3_sym(const double* S, int ld, int m, __nv_bfloat16* s3) {
+    const size_t total = (size_t)m * m;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        const double g = j <= i ? S[(size_t)i * ld + j] : S[(size_t)j * ld + i];
+        __nv_bfloat16 h = bf16_from_double(g);
+        const double r1 = g - (double)__bfloat162float(h);
+        __nv_bfloat16 mid = bf16_from_double(r1);
+        const double r2 = r1 - (double)__bfloat162float(mid);
+        s3[e] = h;
+        s3[total + e] = mid;
+        s3[2 * total + e] = bf16_from_double(r2);
+    }
+}
+
 // ----------------------------------------------------------------- set-up
 
 int setup_case(CaseData& cs, const lgk_case_desc& d) {
@@ -337,7 +355,8 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
 
     // resident footprint check before any large allocation
     size_t resident = (size_t)n_pad + (size_t)m_pad * 8 + 64 +
-                      (bf16 ? (size_t)cs.na * m_pad * n_pad * 2 + (size_t)3 * m_pad * m_pad * 2
+                      (bf16 ? (size_t)cs.na * m_pad * n_pad * 2 +
+                                  (size_t)(cs.prm.solve_refine > 0 ? 6 : 3) * m_pad * m_pad * 2
                             : (size_t)m_pad * n_pad * 4 + (size_t)m_pad * m_pad * 4);
     if (cs.prm.hbm_budget && resident > cs.prm.hbm_budget) {
         set_error("case footprint " + std::to_string(resident) + " B exceeds hbm_budget " +
@@ -438,13 +457,36 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
     }
     LGK_LAUNCH_CHECK();
 
-    // ---- S = A A^T + I (FP64, from the rounded A), Cholesky, inverse
+    // ---- S = A A^T + I from exactly the rounded A, Cholesky, inverse.  BF16
+    // forms: on the tensor cores from the BF16 terms (exact products, FP32
+    // sums of short chunks, FP64 across chunks); FP32 form, or setup_fp64:
+    // FP64 products on the CUDA cores.
     DevBuf S, Y;
+    const bool tc_s = bf16 && !cs.prm.setup_fp64;
+    if (tc_s) {
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        A64.alloc(0);               // the BF16 terms are all the tensor cores need
+    }
     if ((rc = S.alloc((size_t)m_pad * m_pad * 8))) return rc;
-    if ((rc = dgemm_lower_nt(st, m_pad, n_pad, 1.0, A64.as<double>(), n_pad, 0.0, S.as<double>(), m_pad)))
-        return rc;
-    k_add_identity<<<(m_pad + 255) / 256, 256, 0, st>>>(S.as<double>(), m_pad, m_pad);
-    LGK_LAUNCH_CHECK();
+    if (tc_s) {
+        if ((rc = tc_syrk(cs, S.as<double>(), cs.ctrl_setup.as<int>()))) return rc;
+        int e0 = 0;
+        LGK_CUDA_TRY(cudaMemcpy(&e0, cs.ctrl_setup.p, 4, cudaMemcpyDeviceToHost));
+        if (e0) {
+            set_error("tensor-core S = A A^T + I: device error flag " + std::to_string(e0));
+            return LGK_ECUDA;
+        }
+    } else {
+        if ((rc = dgemm_lower_nt(st, m_pad, n_pad, 1.0, A64.as<double>(), n_pad, 0.0, S.as<double>(), m_pad)))
+            return rc;
+        k_add_identity<<<(m_pad + 255) / 256, 256, 0, st>>>(S.as<double>(), m_pad, m_pad);
+        LGK_LAUNCH_CHECK();
+    }
+    if (bf16 && cs.prm.solve_refine > 0) {     // S itself, for the refinement's residual rhs - S v
+        if ((rc = cs.S3.alloc((size_t)m_pad * m_pad * 3 * 2))) return rc;
+        k_split3_sym<<<148 * 8, 256, 0, st>>>(S.as<double>(), m_pad, m_pad, cs.S3.as<__nv_bfloat16>());
+        LGK_LAUNCH_CHECK();
+    }
     LGK_CUDA_TRY(cudaStreamSynchronize(st));
     A64.alloc(0);
 

@@ -34,145 +34,9 @@
 
 #include "iter_ctx.cuh"
 #include "lgk_impl.hpp"
+#include "tc_ptx.cuh"
 
 namespace lgk {
-
-// ------------------------------------------------------------ PTX wrappers
-
-__device__ inline uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ inline uint64_t global_timer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ inline void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after ~2 s of wall time, records DERR_MBAR_TIMEOUT
-// and returns false so the caller can wind down instead of hanging.
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    uint64_t t0 = global_timer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_timer() - t0 > 2000000000ull) {
-            atomicExch(err, DERR_MBAR_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ inline void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
-                                   uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-// The same load with an L2 cache policy (createpolicy) attached.
-__device__ inline void tma_load_3d_hint(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
-                                        uint32_t bar, uint64_t policy) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "l"(policy)
-        : "memory");
-}
-
-// L2 policy for data read once per launch (the streamed A terms): its lines
-// go first, so the operands reused across tiles and kernels stay in L2.
-__device__ inline uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ inline void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-
-__device__ inline void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                              uint32_t accum) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-        : "memory");
-}
-
-__device__ inline void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ inline void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ inline void tmem_ld8(uint32_t taddr, float v[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor (tcgen05 format): start, leading and stride
-// byte offsets in 16-byte units, descriptor version 1, 128-byte swizzle.
-__device__ inline uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;                 // version
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, M = 128, N = n.
-__host__ __device__ constexpr uint32_t instr_desc(int n, bool a_mn_major) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) |
-           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
 
 // term t of an NT-term product: which A part and which B part.
 //   NT = 1: A.B (one part each: the lagged low-term products)
@@ -604,6 +468,11 @@ static int make_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t ro
     return LGK_OK;
 }
 
+int make_tma_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint64_t parts,
+                 uint32_t box_rows) {
+    return make_map(m, base, cols, rows, parts, box_rows);
+}
+
 static constexpr int kSmemLimit = 232448;    // 227 KB opt-in per block
 
 static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 16 + 8 * kChunk * 5 * 4; }
@@ -747,6 +616,10 @@ static int maps_for(ResultData& r, TcMaps& M) {
     if ((rc = make_map(&M.R1, r.R1.p, cs.n_pad, r.Kp, 2, r.n_tile))) return rc;
     if ((rc = make_map(&M.rhs, r.rhs.p, cs.m_pad, r.Kp, 3, r.n_tile_s))) return rc;
     if ((rc = make_map(&M.V, r.V.p, cs.m_pad, r.Kp, 2, r.n_tile))) return rc;
+    if (r.refine_steps) {
+        if ((rc = make_map(&M.S3, cs.S3.p, cs.m_pad, cs.m_pad, 3, 128))) return rc;
+        if ((rc = make_map(&M.V3, r.V3.p, cs.m_pad, r.Kp, 3, r.n_tile_s))) return rc;
+    }
     return LGK_OK;
 }
 
@@ -816,6 +689,11 @@ int tc_gemm1(ResultData& r, bool pdl) {
 
 int tc_solve(ResultData& r, bool pdl) {
     return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr, pdl);
+}
+
+// S v for the solve's refinement: the same product shape as the solve.
+int tc_sv(ResultData& r, bool pdl) {
+    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.S3, r.maps.V3, r.plan_s, r, nullptr, pdl);
 }
 
 int tc_gemm2(ResultData& r, bool pdl) {

@@ -44,13 +44,13 @@ class Params(C.Structure):
                 ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
                 ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int),
-                ("rho_adapt", C.c_int)]
+                ("rho_adapt", C.c_int), ("solve_refine", C.c_int), ("setup_fp64", C.c_int)]
 
 
 class ServerParams(C.Structure):
     _fields_ = [("case_params", Params), ("hbm_budget", C.c_size_t), ("workers", C.c_int),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("w0_bot", C.c_double),
-                ("rho0_per_beta", C.c_double)]
+                ("rho0_per_beta", C.c_double), ("stream_width", C.c_int)]
 
 
 class Pass2Params(C.Structure):
@@ -120,6 +120,12 @@ def _load():
     lib.lgk_server_wait.argtypes = [C.c_void_p, C.c_longlong, C.c_int, P(RequestInfo),
                                     P(C.c_double), P(C.c_double)]
     lib.lgk_server_destroy.argtypes = [C.c_void_p]
+    lib.lgk_server_open.argtypes = [C.c_void_p, P(CaseDesc), P(C.c_longlong)]
+    lib.lgk_server_submit_to.argtypes = [C.c_void_p, C.c_longlong, C.c_int, P(C.c_double),
+                                         P(C.c_longlong)]
+    lib.lgk_server_close.argtypes = [C.c_void_p, C.c_longlong]
+    for f in ("lgk_server_open", "lgk_server_submit_to", "lgk_server_close"):
+        getattr(lib, f).restype = C.c_int
     for f in ("lgk_server_create", "lgk_server_submit", "lgk_server_wait"):
         getattr(lib, f).restype = C.c_int
     lib.lgk_free_result.argtypes = [C.c_void_p]
@@ -483,7 +489,7 @@ def fetch_state(res: Result):
 
 
 KERNELS = ("gemm1", "reduce_rhs", "solve", "reduce_solve", "gemm2", "q1_update", "finalize",
-           "gemm1_lo", "gemm2_lo")
+           "gemm1_lo", "gemm2_lo", "sv", "reduce_err")
 
 
 def fetch_profile(res: Result) -> dict:
@@ -495,16 +501,17 @@ def fetch_profile(res: Result) -> dict:
 
 
 class Server:
-    """Serving loop (lgk_server): requests admitted first come, first served
-    under a device-memory budget, run on worker threads with their own
-    streams."""
+    """Serving loop with continuous batching (lgk_server): resident cases
+    admitted first come, first served under a device-memory budget, each a
+    streaming solve on a worker thread with its own stream; every request for
+    a resident case joins its running stream."""
 
     def __init__(self, *, workers=2, hbm_budget=0, tol=1e-4, max_iter=20000, w0_bot=1e-4,
-                 rho0_per_beta=1.1e3, params: Params | None = None):
+                 rho0_per_beta=1.1e3, stream_width=32, params: Params | None = None):
         sp = ServerParams(case_params=params if params is not None else default_params(),
                           hbm_budget=int(hbm_budget), workers=int(workers), tol=float(tol),
                           max_iter=int(max_iter), w0_bot=float(w0_bot),
-                          rho0_per_beta=float(rho0_per_beta))
+                          rho0_per_beta=float(rho0_per_beta), stream_width=int(stream_width))
         self._h = C.c_void_p()
         _check(_lib.lgk_server_create(C.byref(sp), C.byref(self._h)))
 
@@ -518,6 +525,28 @@ class Server:
                                       C.byref(rid)))
         del keep                     # the library copied everything
         return rid.value
+
+    def open(self, phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2, phi_cal,
+             d_oar=None) -> int:
+        """lgk_server_open: a resident case; returns its case id."""
+        d, keep = _desc(phi, kind, struct_id, n_iso, d_presc, q_area, q_vol, d_ld1, d_ld2,
+                        phi_cal, d_oar)
+        cid = C.c_longlong()
+        _check(_lib.lgk_server_open(self._h, C.byref(d), C.byref(cid)))
+        del keep
+        return cid.value
+
+    def submit_to(self, case_id: int, W) -> int:
+        """lgk_server_submit_to: K weightings for a resident case; returns the request id."""
+        W = np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64)
+        rid = C.c_longlong()
+        _check(_lib.lgk_server_submit_to(self._h, int(case_id), int(W.shape[0]), _ptr(W, C.c_double),
+                                         C.byref(rid)))
+        return rid.value
+
+    def close_case(self, case_id: int) -> None:
+        """lgk_server_close: the case leaves once its queued weightings are done."""
+        _check(_lib.lgk_server_close(self._h, int(case_id)))
 
     def wait(self, rid: int, n_iso: int, K: int, timeout_ms: int = 600000):
         """(info dict, t (K x 24N), tau (K x N)) of request rid."""

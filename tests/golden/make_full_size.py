@@ -3,14 +3,15 @@
 Calls only the oracle (`oracle/`) and the seeded input generator (`synth/`):
 for a sample of slider weightings of the 3750 x 41200 case (81 weightings)
 and of the 5000 x 61600 case (441 weightings) it runs the FP64 literal ADMM
-of Eq. admm to relative residual 1e-6 (100 times tighter than the device's
-1e-4 stop), evaluates the plans' clinical metrics on a regular grid
+of Eq. admm to relative residual 1e-5 (10 times tighter than the device's
+1e-4 stop; columns still above it after 40000 iterations are stored with
+their residuals and flagged), evaluates the plans' clinical metrics on a regular grid
 (Sec. 3.B conventions), the weighted-sum objective of Sec. 2.A at the plans'
 multipliers (the LP's dual objective: weak duality brackets the optimum
 between it and c^T z1), and stores them as JSON.
 
-    python tests/golden/make_full_size.py --cfg 1     # about an hour on 8 cores
-    python tests/golden/make_full_size.py --cfg 2
+    python tests/golden/make_full_size.py --cfg 1     # about an hour on 4 host cores
+    python tests/golden/make_full_size.py --cfg 2     # a few hours (each iteration streams A)
 
 The sampled weightings (indices into `synth.cases.slider_weights(grid)`,
 row-major over (s_LD, s_BOT)) are the four corners of the slider grid, its
@@ -36,7 +37,7 @@ from oracle import lp as L             # noqa: E402
 from oracle import metrics as M        # noqa: E402
 from synth import cases as SC          # noqa: E402
 
-TOL = 1e-6
+TOL = 1e-5
 GRID_SPACING = {1: 2.0, 2: 2.0}        # mm
 GRID_MARGIN = 12.0                     # mm
 
@@ -46,10 +47,37 @@ def sample_indices(g: int) -> list[int]:
     return sorted({0, g - 1, g * (g - 1), g * g - 1, c * g + c, (c // 2) * g + c // 2})
 
 
+def run_chunked(lp, b, l, u, rho, max_iter, t0, chunk=2000):
+    """oracle.admm.admm in chunks of `chunk` iterations on the columns still
+    running, each chunk starting from the state the last one left (the
+    iteration is the same as one long call; the chunks only report
+    progress).  Returns an AdmmResult over all columns."""
+    K = len(rho)
+    n, m = lp.n, lp.m
+    z1, z2, y1, y2 = np.zeros((n, K)), np.zeros((m, K)), np.zeros((n, K)), np.zeros((m, K))
+    x1, x2 = np.zeros((n, K)), np.zeros((m, K))
+    iters = np.zeros(K, dtype=np.int64)
+    conv = np.zeros(K, dtype=bool)
+    rp, rd = np.full(K, np.inf), np.full(K, np.inf)
+    while (~conv).any() and iters.max() < max_iter:
+        a = np.flatnonzero(~conv)
+        r = AD.admm(lp.A, lp.c, b[:, a], l[:, a], u[:, a], rho[a], max_iter=chunk, tol=TOL,
+                    state=(z1[:, a], z2[:, a], y1[:, a], y2[:, a]))
+        z1[:, a], z2[:, a], y1[:, a], y2[:, a] = r.z1, r.z2, r.y1, r.y2
+        x1[:, a], x2[:, a] = r.x1, r.x2
+        iters[a] += r.iters
+        conv[a] = r.converged
+        rp[a], rd[a] = r.rel_pri, r.rel_dual
+        print(f"  {time.time() - t0:.0f} s: iterations {iters.tolist()} converged {int(conv.sum())}/{K} "
+              f"max rel_pri {rp[a].max():.2e} rel_dual {rd[a].max():.2e}", flush=True)
+    return AD.AdmmResult(z1=z1, z2=z2, y1=y1, y2=y2, x1=x1, x2=x2, iters=iters, converged=conv,
+                         rel_pri=rp, rel_dual=rd, rho=np.asarray(rho, dtype=np.float64))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--cfg", type=int, required=True, choices=(1, 2))
-    ap.add_argument("--max-iter", type=int, default=400000)
+    ap.add_argument("--max-iter", type=int, default=40000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     out = a.out or os.path.join(os.path.dirname(os.path.abspath(__file__)),
@@ -65,7 +93,7 @@ def main():
     b, l, u = L.bounds(lp, W)
     print(f"cfg{a.cfg}: A {lp.m} x {lp.n}, beta {lp.beta:.3f}, K {len(idx)}; "
           f"set-up {time.time() - t0:.0f} s", flush=True)
-    res = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=a.max_iter, tol=TOL)
+    res = run_chunked(lp, b, l, u, rho, a.max_iter, t0)
     print(f"ADMM {time.time() - t0:.0f} s, iterations {res.iters.tolist()}, "
           f"converged {res.converged.tolist()}", flush=True)
     lam = res.multipliers()                       # scaled multipliers rho y2 (m x K)
@@ -92,7 +120,7 @@ def main():
         workload=SC.WORKLOADS[a.cfg]["name"], cfg=a.cfg, m=lp.m, n=lp.n, beta=lp.beta,
         rho0=rho0, w0_bot=SC.W0_BOT, tol=TOL, grid=g,
         eval_grid=dict(spacing=GRID_SPACING[a.cfg], margin=GRID_MARGIN, points=int(pts.shape[0])),
-        method="oracle.admm.admm (FP64 literal ADMM, Eq. admm) to relative residual 1e-6; "
+        method="oracle.admm.admm (FP64 literal ADMM, Eq. admm) to relative residual 1e-5; "
                "metrics by oracle.metrics.plan_metrics; planning objective by "
                "oracle.kkt.planning_objective",
         seconds=round(time.time() - t0, 1), plans=rows)

@@ -99,6 +99,10 @@ def test_null_arguments_are_errors_not_crashes(lgk):
     assert lib.lgk_fetch_check(None, None) == 1
     assert lib.lgk_solve_weightings_async(None, 1, None, None, 0.0, 0.0, 0.0, 1, ctypes.byref(h)) == 1
     assert lib.lgk_wait(None, 0) == 1
+    cid = ctypes.c_longlong()
+    assert lib.lgk_server_open(None, None, ctypes.byref(cid)) == 1
+    assert lib.lgk_server_submit_to(None, 0, 1, None, ctypes.byref(cid)) == 1
+    assert lib.lgk_server_close(None, 0) == 1
     lib.lgk_free_result(None)
     lib.lgk_destroy_case(None)
     assert b"NULL" in lib.lgk_last_error() or len(lib.lgk_last_error()) > 0

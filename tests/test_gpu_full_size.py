@@ -1,35 +1,42 @@
-"""GPU checks at full size, in the launch configuration the benchmark times:
-the 3750 x 41200 case (ellipsoid, 150 isocenters, 40000 points), its 81
-slider weightings streamed through 32 columns, slowest (lowest w_BOT) first,
-BF16X3 form with the lagged low term, tol 1e-4.
+"""GPU parity at full size, in the launch configurations the benchmark
+times, against stored oracle plans:
 
-The oracle cannot solve these LPs in a test's time, so the checks are
-properties that hold at any size plus per-plan quantities the oracle
-evaluates one plan at a time in FP64:
-  * every weighting converges (relative residuals <= 1e-4 as reported);
-  * strong duality at the approximate optimum: for sampled plans, the
-    weighted-sum objective of Sec. 2.A evaluated by the oracle at the
-    device's multipliers (sector and isocenter times) equals minus the
-    device's dual objective c^T z to 2e-3 (each side within the 1e-3
-    objective bar; the FP64 oracle ADMM itself reaches <= 6.6e-4 on the
-    9-weighting sphere case at this tolerance);
-  * the hard constraints (BOT coupling tau >= C_S t per isocenter, u = inf
-    columns: (c + A^T lam)_j >= 0) hold to 4 tol ||A||_2 max|lam|: a stop at
-    relative residual tol leaves the multipliers off by about tol relative,
-    and A^T scales that by at most ||A||_2 (32.2 here, 12.0 on the sphere
-    case, where the FP64 oracle ADMM's violation is 1.7e-4 max|lam| against
-    tol ||A||_2 = 1.2e-3).
+  * the 3750 x 41200 ellipsoid case (150 isocenters, 40000 points): its 81
+    slider weightings streamed through 32 columns, lowest BOT weight first;
+  * the 5000 x 61600 four-target case (200 isocenters, 60000 points): its 441
+    weightings streamed through 128 columns;
+
+BF16X3 form with the lagged low term, tol 1e-4 (the benchmark spec's gates).
+
+The stored plans (tests/golden/full_size_cfg{1,2}.json, written by
+tests/golden/make_full_size.py, which calls only the oracle) are the FP64
+literal ADMM of Eq. admm run to relative residual 1e-5 for six weightings of
+each grid, with their clinical metrics on a 2 mm grid over the targets' box
++ 12 mm and the FP64 duality gap that certifies each stored objective.
+Checks:
+  * every weighting converges (relative residuals <= 1e-4) and passes the
+    device's FP64 check against its exact LP: duality gap <= 1e-3, backward
+    error of A z1 <= b at most 1e-4 (lgk_fetch_check);
+  * for the six stored weightings: |obj - obj*| / max(1, |obj*|) <= 1e-3
+    against the oracle's objective, and coverage, selectivity, gradient
+    index and beam-on time of the device's plan (evaluated by the oracle on
+    the same grid from the device's sector times) within 0.5 % of the
+    oracle plan's.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
-from oracle import kkt as KK
 from oracle import lp as L
+from oracle import metrics as M
 from synth import cases as SC
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -43,35 +50,48 @@ def lgk():
     return mod
 
 
-def test_streamed_81_weightings_full_size(lgk):
-    case = SC.workload_case(1)
-    W = SC.slider_weights(SC.WORKLOADS[1]["grid"])
-    W = W[np.argsort(W[:, 3], kind="stable")]
-    lp = L.precondition(L.assemble_case(case))
+def load(cfg):
+    with open(os.path.join(GOLDEN, f"full_size_cfg{cfg}.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("cfg, width", [(1, 32), (2, 128)], ids=["3750x41200_k81", "5000x61600_k441"])
+def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width):
+    gold = load(cfg)
+    case = SC.workload_case(cfg)
+    grid = SC.WORKLOADS[cfg]["grid"]
+    W_all = SC.slider_weights(grid)
+    order = np.argsort(W_all[:, 3], kind="stable")         # lowest BOT weight first
+    W = W_all[order]
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal)
-    assert (cs.m, cs.n) == (lp.m, lp.n) == (3750, 41200)
-    s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=L.rho0_for(lp), tol=TOL, max_iter=20000,
-                         width=32)
+    assert (cs.m, cs.n) == (gold["m"], gold["n"])
+    s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=gold["rho0"], tol=TOL, max_iter=20000,
+                         width=width, check=True)
+    cs.close()
     assert s["converged"].all()
     assert max(s["rel_pri"].max(), s["rel_dual"].max()) <= TOL
+    ck = s["check"]
+    assert np.all(np.abs(ck["gap"]) <= 1e-3), np.abs(ck["gap"]).max()
+    assert np.all(ck["infeas"] <= TOL), ck["infeas"].max()
     assert np.isfinite(s["t"]).all() and (s["t"] >= 0).all() and (s["tau"] >= 0).all()
-    # ||A||_2 by power iteration on A A^T
-    v = np.random.default_rng(0).standard_normal(lp.m)
-    for _ in range(60):
-        v = lp.A @ (lp.A.T @ v)
-        nrm = np.linalg.norm(v)
-        v /= nrm
-    a_norm = np.sqrt(nrm)
-    rng = np.random.default_rng(81)
-    sample = np.unique(np.concatenate([[0, 1, 80], rng.choice(81, size=3, replace=False)]))
-    b, _, u = L.bounds(lp, W[sample])
+
+    pos = {int(w): k for k, w in enumerate(order)}          # grid index -> stream position
+    pts, label, _ = SC.eval_grid(case, spacing=gold["eval_grid"]["spacing"],
+                                 margin=gold["eval_grid"]["margin"])
+    assert pts.shape[0] == gold["eval_grid"]["points"]
+    phi_eval = SC.dose_rate(pts, case.iso)
     rows = []
-    for c, w in enumerate(sample):
-        lam = np.concatenate([s["t"][w], s["tau"][w]]) / lp.row_scale      # scaled multipliers
-        obj, viol = KK.planning_objective(lp.A, b[:, c], lp.c, u[:, c], lam)
-        dual = s["obj"][w]
-        rows.append((int(w), abs(dual + obj) / max(1.0, abs(dual)), viol / np.abs(lam).max()))
-    assert all(g <= 2e-3 for _, g, _ in rows), rows
-    assert all(r <= 4 * TOL * a_norm for _, _, r in rows), (a_norm, rows)
-    cs.close()
+    for g in gold["plans"]:
+        assert g["gap"] <= 1e-4, g                           # the stored optimum is certified
+        k = pos[g["index"]]
+        np.testing.assert_allclose(W[k], g["W"], rtol=0, atol=0)
+        obj = s["obj"][k]
+        gap = abs(obj - g["obj"]) / max(1.0, abs(g["obj"]))
+        t = s["t"][k][:, None]
+        met = M.plan_metrics(M.dose(phi_eval, t), label, case.d_presc, t, case.n_iso)
+        rel = {key: abs(met[key][0] - g[key]) / abs(g[key])
+               for key in ("coverage", "selectivity", "gi", "bot") if g[key] is not None}
+        rows.append((g["index"], gap, rel))
+    assert all(gap <= 1e-3 for _, gap, _ in rows), rows
+    assert all(max(rel.values()) <= 5e-3 for _, _, rel in rows), rows

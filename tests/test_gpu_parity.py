@@ -472,3 +472,33 @@ def test_adaptive_rho_converged_parity(lgk, cfg0):
     fixed = lgk.fetch_stats(lgk.solve_weightings(make(lgk, case, 2), c["W"], c["rho"], tol=TOL,
                                                  max_iter=20000))
     assert st["iters"].mean() <= fixed["iters"].mean(), (st["iters"], fixed["iters"])
+
+
+@pytest.mark.parametrize("prec", [1, 2], ids=["bf16", "bf16x3"])
+def test_tensor_core_schur_complement_matches_fp64(lgk, cfg0, prec):
+    """S = I + A A^T formed on the tensor cores (exact BF16 products, FP32
+    sums of 128-column chunks, FP64 across chunks; the default) against the
+    FP64 product on the CUDA cores (setup_fp64 = 1, exact from the rounded
+    A).  One iteration from the same state: S enters only through S^{-1}, and
+    an entrywise error of ~1e-6 relative in S moves v by ~1e-6 of v, so the
+    two states agree to 1e-5 of their largest entry; and both agree with the
+    oracle within the one-step bound."""
+    c = cfg0
+    A = lp_matrix(c["lp"], lgk, prec)
+    ok = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=300)
+    q1, q2 = (ok.z1 + ok.y1).T, (ok.z2 + ok.y2).T
+    out = []
+    for fp64 in (0, 1):
+        cs = make(lgk, c["case"], prec, lo_refresh=0, setup_fp64=fp64)
+        res = lgk.solve_weightings_warm(cs, c["W"], c["rho"], q1_init=q1, q2_init=q2, tol=0.0, max_iter=1)
+        out.append(lgk.fetch_state(res))
+        cs.close()
+    (a1, a2), (b1, b2) = out
+    assert np.abs(a1 - b1).max() <= 1e-5 * np.abs(b1).max()
+    assert np.abs(a2 - b2).max() <= 1e-5 * np.abs(b2).max()
+    o = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=1,
+                state=(ok.z1, ok.z2, ok.y1, ok.y2))
+    r1, r2 = o.z1 + o.y1, o.z2 + o.y2
+    tol = np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, prec, A.shape[1])
+    assert np.abs(a1.T - r1).max() <= tol * np.abs(r1).max()
+    assert np.abs(a2.T - r2).max() <= tol * np.abs(r2).max()

@@ -81,3 +81,59 @@ def test_admission_budget(lgk):
     # the previous (queue time grows)
     q = [i["queue_ms"] for i in infos]
     assert q[3] > q[0]
+
+
+def test_request_joins_a_running_stream_and_matches_alone(lgk):
+    """Continuous batching: a resident case (lgk_server_open) runs one
+    streaming solve of 8 columns; a 9-weighting request submitted while a
+    25-weighting request of the same case is on the GPU joins that stream
+    (its first weighting takes a column before the other request is done).
+    Its plans equal those of the same request served alone, bit for bit:
+    columns never interact and every column starts the same way."""
+    import time
+    case = small_case(41, 12)
+    W9, W25 = SC.slider_weights(3), SC.slider_weights(5)
+    args = (case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area, case.q_vol,
+            case.d_ld1, case.d_ld2, case.phi_cal)
+    alone = lgk.Server(workers=1, tol=1e-4, stream_width=8)
+    cid = alone.open(*args)
+    rid = alone.submit_to(cid, W9)
+    info_a, t_a, tau_a = alone.wait(rid, case.n_iso, 9)
+    alone.close_case(cid)
+    alone.close()
+    assert info_a["status"] == 0 and info_a["converged"] == 9
+
+    mix = lgk.Server(workers=1, tol=1e-4, stream_width=8)
+    cid = mix.open(*args)
+    t0 = time.perf_counter()
+    big = mix.submit_to(cid, W25)
+    time.sleep(0.05)
+    t1 = time.perf_counter()
+    rid = mix.submit_to(cid, W9)
+    info_m, t_m, tau_m = mix.wait(rid, case.n_iso, 9)
+    info_b, _, _ = mix.wait(big, case.n_iso, 25)
+    mix.close_case(cid)
+    mix.close()
+    assert info_m["status"] == 0 and info_b["status"] == 0
+    assert info_m["converged"] == 9 and info_b["converged"] == 25
+    # the 9-weighting request started while the 25-weighting one was running
+    start_9 = (t1 - t0) * 1e3 + info_m["queue_ms"]
+    assert start_9 < info_b["total_ms"], (start_9, info_b["total_ms"])
+    np.testing.assert_array_equal(t_m, t_a)
+    np.testing.assert_array_equal(tau_m, tau_a)
+    assert info_m["max_iters"] == info_a["max_iters"]
+
+
+def test_closed_case_refuses_requests(lgk):
+    case = small_case(43, 10)
+    srv = lgk.Server(workers=1, tol=1e-4, stream_width=8)
+    cid = srv.open(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                   case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal)
+    rid = srv.submit_to(cid, SC.slider_weights(2))
+    srv.close_case(cid)
+    with pytest.raises(lgk.LgkError) as e:
+        srv.submit_to(cid, SC.slider_weights(2))
+    assert e.value.code == 1
+    info, _, _ = srv.wait(rid, case.n_iso, 4)
+    assert info["status"] == 0 and info["converged"] == 4
+    srv.close()
