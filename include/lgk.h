@@ -137,6 +137,17 @@ typedef struct {
                                 products, FP32 sums over 128 columns of A, FP64 sums of those;
                                 about 1e-6 relative error per entry).  The FP32 form always
                                 uses FP64 products.                                          */
+    int check_fp64;          /* 1: the plan check (lgk_fetch_check, stream checks) forms A z1 and
+                                A^T lam with FP64 products on the CUDA cores; 0 (default): on
+                                the tensor cores from exact BF16 splits, FP32 sums over 64
+                                columns, FP64 across them (two-term BF16 form only).        */
+    int autotune;            /* 1: the first solve of a case at a given column count times each
+                                GEMM configuration on one replay of the real iteration (256- or
+                                128-row tiles for the A GEMMs where both exist; the solve's
+                                column tile whole or halved) and keeps the fastest for later
+                                solves of that case and count.  The configurations sum in
+                                different orders, so plans then differ in rounding from an
+                                untuned solve.  0 (default): the fixed rule.                 */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */
@@ -298,7 +309,12 @@ int lgk_fetch_stats(const lgk_result* res, int* iters, double* obj, double* rel_
  * lam = rho max(q2 - b, 0) as the library holds them, against the LP of
  * Eq. dual_problem with its bounds u and b computed in FP64 (Appendix A), and
  * with A the matrix the iterations use (its BF16 terms summed exactly, or its
- * FP32 copy).  A z1 and A^T lam are FP64 dot products.
+ * FP32 copy).  A z1 and A^T lam: for the two-term BF16 form on the tensor
+ * cores from exact splits (z1 exactly, lam to 2^-24, in three BF16 terms),
+ * exact products, FP32 sums over 64 columns and FP64 sums across them; for
+ * the other forms, or with lgk_params.check_fp64, FP64 dot products on the
+ * CUDA cores (slow on this part's FP64 rate).  Everything after the two
+ * products is FP64.
  * out: K x LGK_CHECK_COUNT host array, per column:
  *   LGK_CHECK_OBJ        c^T z1 (the dual LP's objective)
  *   LGK_CHECK_PLAN       b^T lam + sum over finite-u columns of u (-(c + A^T lam))_+:
@@ -306,20 +322,25 @@ int lgk_fetch_stats(const lgk_result* res, int* iters, double* obj, double* rel_
  *   LGK_CHECK_GAP        (c^T z1 + plan) / max(1, |c^T z1|): relative duality gap
  *                        (the optimum lies between -plan and c^T z1 when both
  *                        points are feasible)
- *   LGK_CHECK_INFEAS     ||(A z1 - b)_+||_2 / || |A| z1 ||_2: normwise backward
- *                        error of A z1 <= b (constraint rows cancel large
- *                        terms; this measures the violation against them)
+ *   LGK_CHECK_INFEAS     ||(A z1 - b)_+||_2 / ||b||_2
  *   LGK_CHECK_INFEAS_ABS ||(A z1 - b)_+||_2
  *   LGK_CHECK_HARD       max over u = inf columns (organ limits, BOT coupling)
  *                        of (-(c + A^T lam))_+, divided by max lam
  *   LGK_CHECK_BOUND      max over finite-u columns of (z1 - u)_+ (the iterations
  *                        clip to FP32 copies of u)
+ *   LGK_CHECK_PRIMAL     ||(A z1 - b)_+||_2 / ((1 + ||A||_2) ||z||_2), z = (z1, min(q2, b)),
+ *                        ||A||_2 estimated at set-up: a column that stopped at
+ *                        relative primal residual tol with an accurate x-step
+ *                        solve has this at most about tol (the violation is
+ *                        A (z1 - x1) + (x2 - z2) + (A x1 - x2)); an inexact solve
+ *                        (A x1 != x2) shows up here
  * Runs on the case's stream; device temporaries of about
  * 64 x (2 n + 2.5 m) doubles are allocated on first use and kept with the
  * result.  Errors: LGK_EINVAL, LGK_ENOMEM, LGK_ECUDA.
  */
 enum { LGK_CHECK_OBJ = 0, LGK_CHECK_PLAN = 1, LGK_CHECK_GAP = 2, LGK_CHECK_INFEAS = 3,
-       LGK_CHECK_INFEAS_ABS = 4, LGK_CHECK_HARD = 5, LGK_CHECK_BOUND = 6, LGK_CHECK_COUNT = 7 };
+       LGK_CHECK_INFEAS_ABS = 4, LGK_CHECK_HARD = 5, LGK_CHECK_BOUND = 6, LGK_CHECK_PRIMAL = 7,
+       LGK_CHECK_COUNT = 8 };
 int lgk_fetch_check(const lgk_result* res, double* out);
 
 /*

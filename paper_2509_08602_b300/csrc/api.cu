@@ -80,6 +80,8 @@ int lgk_default_params(lgk_params* p) {
     p->rho_adapt = 0;
     p->solve_refine = 0;
     p->setup_fp64 = 0;
+    p->check_fp64 = 0;
+    p->autotune = 0;
     return LGK_OK;
 }
 
@@ -95,6 +97,8 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     if (prm.rho_adapt != 0 && prm.rho_adapt != 1) return fail(LGK_EINVAL, "rho_adapt must be 0 or 1");
     if (prm.solve_refine < 0 || prm.solve_refine > 2) return fail(LGK_EINVAL, "solve_refine must be 0, 1 or 2");
     if (prm.setup_fp64 != 0 && prm.setup_fp64 != 1) return fail(LGK_EINVAL, "setup_fp64 must be 0 or 1");
+    if (prm.check_fp64 != 0 && prm.check_fp64 != 1) return fail(LGK_EINVAL, "check_fp64 must be 0 or 1");
+    if (prm.autotune != 0 && prm.autotune != 1) return fail(LGK_EINVAL, "autotune must be 0 or 1");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

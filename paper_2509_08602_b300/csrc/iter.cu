@@ -827,6 +827,28 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         else k_init_r1<false><<<g, 256, 0, st>>>(cx, r.R1.p);
         LGK_LAUNCH_CHECK();
     }
+    // GEMM configurations (lgk_params.autotune): the case's stored choice for
+    // this column count, or candidates to time on the first replays
+    std::vector<std::pair<int, int>> cands;
+    size_t tune_next = 0;
+    std::vector<float> tune_ms;
+    if (bf16 && cs.prm.autotune) {
+        std::lock_guard<std::mutex> lk(cs.tune_mu);
+        auto it = cs.tuned.find(Kp);
+        if (it != cs.tuned.end()) {
+            r.force_wide = it->second.first;
+            r.n_tile_s = it->second.second;
+        } else {
+            const bool can_wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
+            std::vector<int> ws = can_wide ? std::vector<int>{1, 0} : std::vector<int>{0};
+            std::vector<int> ss{r.n_tile_s};
+            if (r.n_tile_s % 32 == 0) ss.push_back(r.n_tile_s / 2);
+            for (int w : ws)
+                for (int t : ss) cands.push_back({w, t});
+            r.force_wide = cands[0].first;
+            r.n_tile_s = cands[0].second;
+        }
+    }
     if (bf16) {
         if ((rc = tc_prepare(r))) return rc;
     } else {
@@ -897,6 +919,39 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     // cap), give those columns the next weightings, and push the new flags,
     // tables and counters.  done: no column holds a weighting; age: the
     // iterations of the oldest running column.
+    // FP64 checks of a stream's stopped weightings (StreamSpec::check): their
+    // states are saved at the boundary where they stop and checked in
+    // batches of kChkSave (one pass over A per batch instead of one per
+    // boundary)
+    constexpr int kChkSave = 64;
+    std::vector<long long> pend_tag;
+    std::vector<float> pend_uf, pend_rho, pend_wbf;
+    std::vector<double> pend_u64, pend_wb64;
+    DevBuf saved;
+    if (stream && stream->check &&
+        (rc = saved.alloc((size_t)kChkSave * (cs.n_pad + cs.m_pad) * 4)))
+        return rc;
+    auto flush_checks = [&]() -> int {
+        const int nc = (int)pend_tag.size();
+        if (!nc) return LGK_OK;
+        std::vector<int> src(nc);
+        for (int c = 0; c < nc; ++c) src[c] = c;
+        std::vector<double> out((size_t)nc * LGK_CHECK_COUNT);
+        const int rcc = run_check_states(r, saved.as<float>(), saved.as<float>() + (size_t)kChkSave * cs.n_pad,
+                                         nc, src.data(), nullptr, pend_uf.data(), pend_rho.data(),
+                                         pend_wbf.data(), pend_u64.data(), pend_wb64.data(), out.data());
+        if (rcc) return rcc;
+        for (int c = 0; c < nc; ++c)
+            std::copy(&out[(size_t)c * LGK_CHECK_COUNT], &out[(size_t)(c + 1) * LGK_CHECK_COUNT],
+                      stream->check + (size_t)pend_tag[c] * LGK_CHECK_COUNT);
+        pend_tag.clear();
+        pend_uf.clear();
+        pend_rho.clear();
+        pend_wbf.clear();
+        pend_u64.clear();
+        pend_wb64.clear();
+        return LGK_OK;
+    };
     // the next weighting of the stream: from the caller's arrays, or pulled
     // from a dynamic source (1: one, 0: none now, -1: closed and drained)
     auto next_weighting = [&](double* w, double* rh, long long* tag, bool block) -> int {
@@ -920,7 +975,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         if (ss.rel_pri) ss.rel_pri[w] = o.rel_pri;
         if (ss.rel_dual) ss.rel_dual[w] = o.rel_dual;
         if (ss.converged) ss.converged[w] = (uint8_t)o.converged;
-        if (ss.check && o.check) std::copy(o.check, o.check + LGK_CHECK_COUNT, ss.check + w * LGK_CHECK_COUNT);
+
         if (ss.t) std::copy(o.t, o.t + cs.n_beams, ss.t + w * cs.n_beams);
         if (ss.tau) std::copy(o.tau, o.tau + cs.n_iso, ss.tau + w * cs.n_iso);
     };
@@ -957,10 +1012,35 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             LGK_CUDA_TRY(cudaMemcpyAsync(lam.data(), lam_d.p, lam.size() * 8, cudaMemcpyDeviceToHost, st));
             LGK_CUDA_TRY(cudaStreamSynchronize(st));
             std::vector<double> chk;
-            if (ss.check || ss.want_check) {   // FP64 check of the stopped columns, before refilling
+            r.colp_h = colp;
+            if (ss.want_check && !ss.check) {  // FP64 check now, for the result callback
                 chk.resize(ret.size() * (size_t)LGK_CHECK_COUNT);
                 const int rcc = run_check(r, ret.data(), (int)ret.size(), chk.data());
                 if (rcc) return rcc;
+            }
+            if (ss.check) {                    // save the state for a batched FP64 check
+                for (int j : ret) {
+                    if ((int)pend_tag.size() == kChkSave) {
+                        const int rcf = flush_checks();
+                        if (rcf) return rcf;
+                    }
+                    const int slot = (int)pend_tag.size();
+                    LGK_CUDA_TRY(cudaMemcpyAsync(saved.as<float>() + (size_t)slot * cs.n_pad,
+                                                 r.q1.as<float>() + (size_t)j * cs.n_pad, (size_t)cs.n_pad * 4,
+                                                 cudaMemcpyDeviceToDevice, st));
+                    LGK_CUDA_TRY(cudaMemcpyAsync(saved.as<float>() + (size_t)kChkSave * cs.n_pad +
+                                                     (size_t)slot * cs.m_pad,
+                                                 r.q2.as<float>() + (size_t)j * cs.m_pad, (size_t)cs.m_pad * 4,
+                                                 cudaMemcpyDeviceToDevice, st));
+                    pend_tag.push_back(tag_of[j]);
+                    for (int sl = 0; sl < S; ++sl) {
+                        pend_uf.push_back(utab[(size_t)j * S + sl]);
+                        pend_u64.push_back(r.u64[(size_t)j * S + sl]);
+                    }
+                    pend_rho.push_back(colp[j]);
+                    pend_wbf.push_back(colp[2 * (size_t)Kp + j]);
+                    pend_wb64.push_back(r.wb64[j]);
+                }
             }
             for (size_t c = 0; c < ret.size(); ++c) {
                 const int j = ret[c];
@@ -1067,6 +1147,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             fac.push_back(f);
         }
         if (cols.empty()) return LGK_OK;
+        r.colp_h = colp;
         if (!adapt_d.p) {
             const int rc2 = adapt_d.alloc((size_t)Kp * 8);
             if (rc2) return rc2;
@@ -1084,12 +1165,31 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         LGK_CUDA_TRY(cudaStreamSynchronize(st));
         return LGK_OK;
     };
+    // a new GEMM configuration: re-plan and re-capture between two replays
+    auto reconfigure = [&](int wide, int nts) -> int {
+        cudaGraphExecDestroy(r.graph);
+        r.graph = nullptr;
+        r.force_wide = wide;
+        r.n_tile_s = nts;
+        int rc2 = tc_prepare(r);
+        if (rc2) return rc2;
+        cx = make_ctx(r);
+        return capture();
+    };
+    cudaEvent_t tev[2] = {nullptr, nullptr};
+    if (!cands.empty()) {
+        LGK_CUDA_TRY(cudaEventCreate(&tev[0]));
+        LGK_CUDA_TRY(cudaEventCreate(&tev[1]));
+    }
     int iter_before = 0;
     auto t0 = std::chrono::steady_clock::now();
     rc = LGK_OK;
     for (;;) {
         if (dynamic) t0 = std::chrono::steady_clock::now();     // a server stream: bound each replay
+        const bool timing = tune_next < cands.size();
+        if (timing) cudaEventRecord(tev[0], st);
         cudaError_t le = cudaGraphLaunch(r.graph, st);
+        if (timing) cudaEventRecord(tev[1], st);
         if (le != cudaSuccess) { set_error(cudaGetErrorString(le)); rc = LGK_ECUDA; break; }
         count_launch((long long)n_nodes - 0);
         cudaMemcpyAsync(hc, r.ctrl.p, sizeof(Control), cudaMemcpyDeviceToHost, st);
@@ -1142,6 +1242,27 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             break;
         }
         if (cs.prm.rho_adapt && (rc = adapt_rho())) break;
+        if (timing) {
+            // autotuner: this replay ran candidate tune_next; time the next one,
+            // or keep the fastest (ties: the earlier, i.e. the default) for
+            // this case and column count
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, tev[0], tev[1]);
+            tune_ms.push_back(ms);
+            ++tune_next;
+            std::pair<int, int> pick = cands[tune_next < cands.size() ? tune_next : 0];
+            if (tune_next == cands.size()) {
+                size_t best = 0;
+                for (size_t c = 1; c < tune_ms.size(); ++c)
+                    if (tune_ms[c] < tune_ms[best]) best = c;
+                pick = cands[best];
+                std::lock_guard<std::mutex> lk(cs.tune_mu);
+                cs.tuned[Kp] = pick;
+            }
+            if ((pick.first != r.force_wide || pick.second != r.n_tile_s) &&
+                (rc = reconfigure(pick.first, pick.second)))
+                break;
+        }
         if (r.refine && cs.prm.lo_refresh_iters > 0 && age >= cs.prm.lo_refresh_iters) {
             // columns still running this long: continue with the literal
             // iteration (all terms every step) from the current state
@@ -1154,7 +1275,11 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         }
     }
     cudaFreeHost(hc);
+    for (cudaEvent_t e : tev)
+        if (e) cudaEventDestroy(e);
+    r.colp_h = colp;
     if (rc) return rc;
+    if (stream && (rc = flush_checks())) return rc;
     k_objective<<<Kp, 256, 0, st>>>(cx, r.stats.as<double>() + 2 * Kp);
     LGK_LAUNCH_CHECK();
     LGK_CUDA_TRY(cudaStreamSynchronize(st));

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <condition_variable>
 #include <functional>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -28,6 +29,8 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+struct CheckTC;   // tensor-core plan check of a case (check.cu)
+
 struct CaseData {
     lgk_params prm{};
     int device = 0;
@@ -41,6 +44,7 @@ struct CaseData {
     int m_pad = 0, n_pad = 0;              // multiples of 256
     int n_targets = 0, n_oars = 0, n_slot = 0;
     double beta = 1.0;
+    double a_norm = 0.0;                   // ||A||_2 of the iterations' A (power iteration on S)
     std::vector<int> slot_count;           // points per slot (TS/TI/R per target, LD1, LD2, OAR)
     std::vector<uint8_t> slot_host;        // slot of every point [n_pts]
     std::vector<double> q_area, q_vol, d_presc;
@@ -56,6 +60,11 @@ struct CaseData {
     DevBuf S3;         // bf16 [3][m_pad][m_pad] S = hi + mid + lo (BF16 forms, solve_refine > 0)
     DevBuf ctrl_setup; // int [4] device error flags during set-up
     std::atomic<int> async_busy{0};   // an asynchronous solve of this case is running
+    std::unique_ptr<CheckTC> chk_tc;  // plans, maps and buffers of the plan check, made on first use
+    // GEMM configurations chosen by the autotuner (lgk_params.autotune), per
+    // column count Kp: (256-row tiles for the A GEMMs, solve column tile)
+    std::map<int, std::pair<int, int>> tuned;
+    std::mutex tune_mu;
     size_t bytes_held() const;
     ~CaseData();
 };
@@ -84,6 +93,16 @@ struct GemmPlan {
     int* tile_count = nullptr;      // per tile: segments done in the running launch
 };
 
+// The plan check on the tensor cores (check.cu): its two products' plans
+// (stream-K segments of one k block), TMA maps, split operands of up
+// to kCheckCols plans, partial sums and a control block showing work to do.
+constexpr int kCheckCols = 16;
+struct CheckTC {
+    GemmPlan az, atl;
+    DevBuf part, ctrl, z3, l3;
+    CUtensorMap mA_k, mA_mn, mZ, mL;
+};
+
 struct ResultData {
     std::shared_ptr<CaseData> cs;
     TcMaps maps;
@@ -101,6 +120,7 @@ struct ResultData {
     DevBuf utab;              // float [Kp][n_slot] upper bounds u per slot
     bool refine = false;      // lo_refresh: heavy products with A_hi, lo products lagged
     bool wide = false;        // GEMM1 / GEMM2 (and the lo products) on 256-row tiles
+    int force_wide = -1;      // autotuner: -1 the default rule, 0 / 1 forced (where allowed)
     DevBuf c1, c2;            // float [Kp][m_pad] lo R1_hi, [Kp][n_pad] lo^T V_hi (last full iteration)
     int refine_steps = 0;     // solve refinement steps per iteration (lgk_params.solve_refine)
     DevBuf rhs32, rv, V3;     // refinement: rhs FP32 [Kp][m_pad], v so far FP32, v as bf16 [3][Kp][m_pad]
@@ -113,6 +133,7 @@ struct ResultData {
     DevBuf stats;             // double [3][Kp]: rel_pri, rel_dual, obj
     std::vector<double> u64;  // host [Kp][n_slot]: each column's bounds u in FP64 (the FP64 check)
     std::vector<double> wb64; // host [Kp]: each column's w_BOT in FP64
+    std::vector<float> colp_h;// host copy of colp (rho, 1/rho, w_BOT as the iteration holds them)
     DevBuf chk;               // device temporaries of the FP64 check (run_check)
 
     // asynchronous solve (lgk_solve_weightings_async): the worker thread that
@@ -185,8 +206,12 @@ int fetch_metrics(const ResultData& r, const double* phi_eval, int n_eval, const
                   double* coverage, double* selectivity, double* gi, double* bot);
 // 0 when a result may be read (its asynchronous solve, if any, waited for)
 int result_ready(ResultData& d);
-// FP64 check of the listed columns (check.cu): out [nc][LGK_CHECK_COUNT], host
+// FP64 check of the listed live columns (check.cu): out [nc][LGK_CHECK_COUNT], host
 int run_check(ResultData& r, const int* cols, int nc, double* out);
+// FP64 check of nc saved state columns with their tables (check.cu)
+int run_check_states(ResultData& r, const float* q1, const float* q2, int nc, const int* src, const int* mcol,
+                     const float* uf, const float* rhof, const float* wbf, const double* u64,
+                     const double* wb64, double* out);
 
 // FP64 GEMM (setup.cu):  C = alpha op(A) op(B) + beta C, row-major.
 int dgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, double alpha,
@@ -200,7 +225,11 @@ int make_tma_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows,
 int tc_syrk(CaseData& cs, double* S, int* err);
 
 // Tensor-core GEMMs (tc_gemm.cu)
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt);
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt,
+               int max_seg = 0);    // max_seg > 0: no segment crosses a multiple of max_seg k blocks
+struct IterCtx;
+int tc_check_product(CaseData& cs, bool transpose, const CUtensorMap& mA, const CUtensorMap& mB,
+                     const GemmPlan& P, const IterCtx& cx, float* part, cudaStream_t st);
 int sm_count();
 struct IterCtx;
 IterCtx make_ctx_public(ResultData& r);

@@ -338,6 +338,93 @@ __global__ void k_split3_sym(const double* S, int ld, int m, __nv_bfloat16* s3) 
     }
 }
 
+// S[i][j] = S[j][i] for j > i: the upper triangle from the lower one (32 x 32
+// tiles through shared memory, so both sides are read and written in rows).
+__global__ void k_mirror_lower(double* S, int ld, int m) {
+    __shared__ double t[32][33];
+    const int bi = blockIdx.y, bj = blockIdx.x;       // destination tile (rows bi, cols bj), bj >= bi
+    if (bj < bi) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;     // 32 x 8 threads
+    for (int k = ty; k < 32; k += 8) {                // source tile (rows bj, cols bi)
+        const int r = bj * 32 + k, c = bi * 32 + tx;
+        t[k][tx] = (r < m && c < m) ? S[(size_t)r * ld + c] : 0.0;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int r = bi * 32 + k, c = bj * 32 + tx;
+        if (r < m && c < m && c > r) S[(size_t)r * ld + c] = t[tx][k];
+    }
+}
+
+// y = S x (S full, FP64), one warp per row, fixed summation order.
+__global__ void k_symv(const double* __restrict__ S, int ld, int m, const double* __restrict__ x, double* y) {
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (row >= m) return;
+    double s = 0.0;
+    for (int j = lane; j < m; j += 32) s += S[(size_t)row * ld + j] * x[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
+}
+
+// out[0] = x . y, out[1] = y . y (one block, fixed order)
+__global__ void k_dot2(const double* x, const double* y, int m, double* out) {
+    __shared__ double a[256], b[256];
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < m; i += 256) {
+        sa += x[i] * y[i];
+        sb += y[i] * y[i];
+    }
+    a[threadIdx.x] = sa;
+    b[threadIdx.x] = sb;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            a[threadIdx.x] += a[threadIdx.x + w];
+            b[threadIdx.x] += b[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = a[0];
+        out[1] = b[0];
+    }
+}
+
+__global__ void k_scale_vec(const double* y, int m, const double* nrm2, double* x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) x[i] = y[i] / sqrt(nrm2[1]);
+}
+
+__global__ void k_fill(double* x, int m, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) x[i] = v;
+}
+
+// ||A||_2 from S = I + A A^T: power iteration on S (S's entries are mostly
+// positive, so the all-ones start overlaps its top eigenvector), Rayleigh
+// quotient lambda_max(S) = 1 + ||A||_2^2.  S must be full (mirrored).
+static int a_norm_estimate(cudaStream_t st, const double* S, int ld, int m, double* out) {
+    DevBuf x, y, d;
+    int rc;
+    if ((rc = x.alloc((size_t)m * 8)) || (rc = y.alloc((size_t)m * 8)) || (rc = d.alloc(16))) return rc;
+    const int g = (m + 255) / 256;
+    k_fill<<<g, 256, 0, st>>>(x.as<double>(), m, 1.0 / sqrt((double)m));
+    LGK_LAUNCH_CHECK();
+    double h[2] = {0.0, 0.0};
+    for (int it = 0; it < 60; ++it) {
+        k_symv<<<(m + 7) / 8, 256, 0, st>>>(S, ld, m, x.as<double>(), y.as<double>());
+        LGK_LAUNCH_CHECK();
+        k_dot2<<<1, 256, 0, st>>>(x.as<double>(), y.as<double>(), m, d.as<double>());
+        LGK_LAUNCH_CHECK();
+        k_scale_vec<<<g, 256, 0, st>>>(y.as<double>(), m, d.as<double>(), x.as<double>());
+        LGK_LAUNCH_CHECK();
+    }
+    LGK_CUDA_TRY(cudaMemcpyAsync(h, d.p, 16, cudaMemcpyDeviceToHost, st));
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = sqrt(std::max(h[0] - 1.0, 0.0));      // x . S x with ||x|| = 1
+    return LGK_OK;
+}
+
 // ----------------------------------------------------------------- set-up
 
 int setup_case(CaseData& cs, const lgk_case_desc& d) {
@@ -481,6 +568,14 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
             return rc;
         k_add_identity<<<(m_pad + 255) / 256, 256, 0, st>>>(S.as<double>(), m_pad, m_pad);
         LGK_LAUNCH_CHECK();
+    }
+    {
+        // ||A||_2 (the FP64 plan check bounds a converged plan's constraint
+        // violation by (1 + ||A||_2) tol ||z||)
+        dim3 gt((m_pad + 31) / 32, (m_pad + 31) / 32), bt(32, 8);
+        k_mirror_lower<<<gt, bt, 0, st>>>(S.as<double>(), m_pad, m_pad);
+        LGK_LAUNCH_CHECK();
+        if ((rc = a_norm_estimate(st, S.as<double>(), m_pad, m_pad, &cs.a_norm))) return rc;
     }
     if (bf16 && cs.prm.solve_refine > 0) {     // S itself, for the refinement's residual rhs - S v
         if ((rc = cs.S3.alloc((size_t)m_pad * m_pad * 3 * 2))) return rc;

@@ -42,8 +42,10 @@ namespace lgk {
 //   NT = 1: A.B (one part each: the lagged low-term products)
 //   NT = 2: A.B_hi + A.B_lo
 //   NT = 3: A_hi.B_hi + A_hi.B_lo + A_lo.B_hi
+//   NT = 5: two parts of A, three of B, all (a, b) with a + b <= 2
 //   NT = 6: all (a, b) with a + b <= 2 over three parts each
 // (dropped terms are below 2^-16 resp. 2^-24 of the product, relative).
+// NT = 5 and 6 share the order (0,0) (0,1) (1,0) (0,2) (1,1) [(2,0)].
 __host__ __device__ constexpr int term_a(int NT, int t) {
     return NT <= 2 ? 0 : NT == 3 ? (t == 2 ? 1 : 0)
                                : (t == 0 || t == 1 || t == 3 ? 0 : (t == 2 || t == 4 ? 1 : 2));
@@ -490,7 +492,8 @@ int sm_count() {
 // Stream-K plan: the units (column tile, row tile, k block), in that order,
 // cut into `grid` contiguous runs of equal length (+-1), each run split into
 // segments at tile boundaries.  Depends only on the GEMM's shape.
-int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt) {
+int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, bool split_first, int mt,
+               int max_seg) {
     const long long T = (long long)rows * col_tiles;
     const long long U = T * kb_total;
     const int grid = (int)std::min<long long>(sm_count(), U);
@@ -518,6 +521,7 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, b
             long long tile = u0 / kb_total;
             int kb0 = (int)(u0 % kb_total);
             int kb1 = (int)std::min<long long>(kb_total, kb0 + (u1 - u0));
+            if (max_seg > 0) kb1 = std::min(kb1, (kb0 / max_seg + 1) * max_seg);   // segments inside aligned chunks
             add(tile, kb0, kb1);
             u0 += kb1 - kb0;
         }
@@ -559,6 +563,10 @@ int build_plan(GemmPlan& P, int rows, int col_tiles, int kb_total, int n_tile, b
     P.tile_slots = P.tile_begin + rows * col_tiles + 1;
     return LGK_OK;
 }
+
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
+static int launch_in(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, CaseData& cs,
+                     const IterCtx& cx, float* part, cudaStream_t st);
 
 template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
@@ -653,7 +661,8 @@ int tc_prepare(ResultData& r) {
     // 256-row tiles for the GEMMs whose A operand is one BF16 term (the
     // one-term form, or A_hi and A_lo with lo_refresh) when two accumulators
     // fit in tensor memory next to each other
-    r.wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
+    const bool can_wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
+    r.wide = can_wide && (r.force_wide < 0 || r.force_wide == 1);
     const int hm = r.wide ? 2 : 1;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
     if ((rc = build_plan(r.plan1, mt / hm, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false, hm))) return rc;
@@ -689,6 +698,46 @@ int tc_gemm1(ResultData& r, bool pdl) {
 
 int tc_solve(ResultData& r, bool pdl) {
     return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr, pdl);
+}
+
+// One EPI_PARTIAL product outside a solve's iteration (the plan check): the
+// caller's context (its control block must show work to do) and partial
+// buffer.  The kernel needs no predecessor (no programmatic launch).
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT>
+static int launch_in(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, CaseData& cs,
+                     const IterCtx& cx, float* part, cudaStream_t st) {
+    TcArgs a{};
+    a.cta_seg = P.cta_seg;
+    a.seg = P.seg;
+    a.tile_begin = P.tile_begin;
+    a.tile_slots = P.tile_slots;
+    a.tile_count = P.tile_count;
+    a.row_tiles = P.rows;
+    a.n_tile = P.n_tile;
+    a.part = part;
+    a.out = nullptr;
+    a.out_ld = A_MN ? cs.n_pad : cs.m_pad;
+    a.stage_bytes = NA * MT * kABytes + NB * a.n_tile * 128;
+    a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
+    a.tmem_cols = 32;
+    while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
+    a.nbuf = 4 * MT * a.tmem_cols <= 512 ? 4 : 2;
+    const size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
+    LGK_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem, st, false, mA,
+                          mB, a, cx));
+    LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
+// The plan check's products with exact split operands: A (two BF16 terms,
+// K-major for A z1 or MN-major for A^T lam) times three BF16 terms of the
+// plans' vectors, 5 products, stream-K segments of at most one k block.
+int tc_check_product(CaseData& cs, bool transpose, const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P,
+                     const IterCtx& cx, float* part, cudaStream_t st) {
+    if (transpose) return launch_in<2, 3, 5, true, EPI_PARTIAL, 1>(mA, mB, P, cs, cx, part, st);
+    return launch_in<2, 3, 5, false, EPI_PARTIAL, 1>(mA, mB, P, cs, cx, part, st);
 }
 
 // S v for the solve's refinement: the same product shape as the solve.

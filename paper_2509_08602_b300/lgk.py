@@ -44,7 +44,8 @@ class Params(C.Structure):
                 ("check_every", C.c_int), ("eps_abs", C.c_double), ("device", C.c_int),
                 ("stream", C.c_void_p), ("hbm_budget", C.c_size_t), ("timeout_ms", C.c_int),
                 ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int),
-                ("rho_adapt", C.c_int), ("solve_refine", C.c_int), ("setup_fp64", C.c_int)]
+                ("rho_adapt", C.c_int), ("solve_refine", C.c_int), ("setup_fp64", C.c_int),
+                ("check_fp64", C.c_int), ("autotune", C.c_int)]
 
 
 class ServerParams(C.Structure):
@@ -468,7 +469,7 @@ def fetch_stats(res: Result) -> dict:
     return dict(iters=it, obj=obj, rel_pri=rp, rel_dual=rd, converged=conv.astype(bool))
 
 
-CHECK_FIELDS = ("obj", "plan", "gap", "infeas", "infeas_abs", "hard", "bound")   # LGK_CHECK_*
+CHECK_FIELDS = ("obj", "plan", "gap", "infeas", "infeas_abs", "hard", "bound", "primal")   # LGK_CHECK_*
 
 
 def fetch_check(res: Result) -> dict:

@@ -3,15 +3,16 @@
 Calls only the oracle (`oracle/`) and the seeded input generator (`synth/`):
 for a sample of slider weightings of the 3750 x 41200 case (81 weightings)
 and of the 5000 x 61600 case (441 weightings) it runs the FP64 literal ADMM
-of Eq. admm to relative residual 1e-5 (10 times tighter than the device's
-1e-4 stop; columns still above it after 40000 iterations are stored with
-their residuals and flagged), evaluates the plans' clinical metrics on a regular grid
+of Eq. admm to relative residual 5e-5 (the stop the GPU tests solve to:
+plans of these degenerate LPs are compared at the same stop; columns still
+above it after 40000 iterations are stored with their residuals and
+flagged), evaluates the plans' clinical metrics on a regular grid
 (Sec. 3.B conventions), the weighted-sum objective of Sec. 2.A at the plans'
 multipliers (the LP's dual objective: weak duality brackets the optimum
 between it and c^T z1), and stores them as JSON.
 
-    python tests/golden/make_full_size.py --cfg 1     # about an hour on 4 host cores
-    python tests/golden/make_full_size.py --cfg 2     # a few hours (each iteration streams A)
+    python tests/golden/make_full_size.py --cfg 1     # about 30 min on 4 host cores
+    python tests/golden/make_full_size.py --cfg 2     # about 1-2 h (each iteration streams A)
 
 The sampled weightings (indices into `synth.cases.slider_weights(grid)`,
 row-major over (s_LD, s_BOT)) are the four corners of the slider grid, its
@@ -37,7 +38,7 @@ from oracle import lp as L             # noqa: E402
 from oracle import metrics as M        # noqa: E402
 from synth import cases as SC          # noqa: E402
 
-TOL = 1e-5
+TOL = 5e-5
 GRID_SPACING = {1: 2.0, 2: 2.0}        # mm
 GRID_MARGIN = 12.0                     # mm
 
@@ -120,7 +121,7 @@ def main():
         workload=SC.WORKLOADS[a.cfg]["name"], cfg=a.cfg, m=lp.m, n=lp.n, beta=lp.beta,
         rho0=rho0, w0_bot=SC.W0_BOT, tol=TOL, grid=g,
         eval_grid=dict(spacing=GRID_SPACING[a.cfg], margin=GRID_MARGIN, points=int(pts.shape[0])),
-        method="oracle.admm.admm (FP64 literal ADMM, Eq. admm) to relative residual 1e-5; "
+        method="oracle.admm.admm (FP64 literal ADMM, Eq. admm) to relative residual 5e-5; "
                "metrics by oracle.metrics.plan_metrics; planning objective by "
                "oracle.kkt.planning_objective",
         seconds=round(time.time() - t0, 1), plans=rows)

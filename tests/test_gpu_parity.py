@@ -32,6 +32,16 @@ from device_model import lagged_admm
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
+# Converged solves stop at 5e-5: a stop at relative residual 1e-4 leaves the
+# objective within about 1e-3 of the optimum, not below it (one weighting of
+# the BF16X3 form stops at 1.01e-3 to 1.05e-3, depending on the rounding
+# order of S), so solving to 5e-5 meets both the benchmark spec gates (residuals
+# <= 1e-4, objective gap <= 1e-3) with headroom.  The oracle reference plans
+# stop at the same tolerance: these LPs are degenerate in the sector times
+# (plans are compared with the oracle's ADMM plan from the same start and
+# stop, not with a vertex), and a plan stopped at 1e-4 differs from one at
+# 5e-5 by up to 1.8 % in beam-on time.
+SOLVE_TOL = TOL / 2
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +63,7 @@ def cfg0():
     b, l, u = L.bounds(lp, W)
     rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     opt = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(W.shape[0])])
-    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=TOL)
+    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=20000, tol=SOLVE_TOL)
     pts, label, _ = SC.eval_grid(case, spacing=1.0, margin=12.0)
     phi_eval = SC.dose_rate(pts, case.iso)
     t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
@@ -172,14 +182,14 @@ def test_converged_parity_cfg0(lgk, cfg0, prec):
     if prec == lgk.PREC_BF16:        # its own LP: the oracle on the rounded matrix
         A = lp_matrix(lp, lgk, prec)
         opt = np.array([SX.simplex(A, c["b"][:, j], lp.c, c["u"][:, j]).obj for j in range(9)])
-        ref = AD.admm(A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=TOL)
+        ref = AD.admm(A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=SOLVE_TOL)
         t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
         met_ref = M.plan_metrics(M.dose(c["phi_eval"], t_ref), c["label"], case.d_presc, t_ref,
                                  case.n_iso)
     else:
         opt, met_ref = c["opt"], c["met_ref"]
     cs = make(lgk, case, prec)
-    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=SOLVE_TOL, max_iter=20000)
     st = lgk.fetch_stats(res)
     assert st["converged"].all()
     gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
@@ -339,7 +349,7 @@ def test_oar_and_unequal_prescriptions(lgk):
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
                          case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal, d_oar=case.d_oar,
                          params=lgk.default_params(precision=lgk.PREC_BF16X3))
-    res = lgk.solve_weightings(cs, W, rho, tol=TOL, max_iter=30000)
+    res = lgk.solve_weightings(cs, W, rho, tol=SOLVE_TOL, max_iter=30000)
     st = lgk.fetch_stats(res)
     assert st["converged"].all()
     gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
@@ -347,7 +357,7 @@ def test_oar_and_unequal_prescriptions(lgk):
     t, _ = lgk.fetch_times(res)
     oar_pts = case.phi[case.kind == SC.KIND_OAR]
     assert np.all((oar_pts @ t.T).max(0) <= d_o * 1.005)
-    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=30000, tol=TOL)
+    ref = AD.admm(lp.A, lp.c, b, l, u, rho, max_iter=30000, tol=SOLVE_TOL)
     t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
     pts, label, _ = SC.eval_grid(case, spacing=1.0, margin=12.0)
     phi_eval = SC.dose_rate(pts, case.iso)
@@ -365,7 +375,7 @@ def test_lagged_iteration_gives_way_to_the_literal_one(lgk, cfg0):
     graph, the same state) and converges to the same plans."""
     c = cfg0
     cs = make(lgk, c["case"], 2, lo_refresh_iters=30, profile=1)
-    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=SOLVE_TOL, max_iter=20000)
     st = lgk.fetch_stats(res)
     assert st["converged"].all()
     gap = np.abs(st["obj"] - c["opt"]) / np.maximum(1.0, np.abs(c["opt"]))
@@ -406,7 +416,7 @@ def test_stream_refills_columns_and_matches_the_batch(lgk, cfg0):
     batch solve's up to the shifted low-term refresh points."""
     c = cfg0
     cs = make(lgk, c["case"], 2)
-    rule = dict(w0_bot=SC.W0_BOT, rho0=L.rho0_for(c["lp"]), tol=TOL, max_iter=20000)
+    rule = dict(w0_bot=SC.W0_BOT, rho0=L.rho0_for(c["lp"]), tol=SOLVE_TOL, max_iter=20000)
     s = lgk.solve_stream(cs, c["W"], width=4, **rule)
     assert s["converged"].all()
     assert max(s["rel_pri"].max(), s["rel_dual"].max()) <= TOL
@@ -451,13 +461,13 @@ def test_adaptive_rho_converged_parity(lgk, cfg0):
     the fixed-penalty one."""
     c = cfg0
     case, lp = c["case"], c["lp"]
-    ref = AD.admm(lp.A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=TOL,
+    ref = AD.admm(lp.A, lp.c, c["b"], c["l"], c["u"], c["rho"], max_iter=20000, tol=SOLVE_TOL,
                   balance=(50, 3.0, 1.5, 40))
     assert ref.converged.all()
     t_ref, _ = L.times_from_multipliers(lp, ref.multipliers())
     met_ref = M.plan_metrics(M.dose(c["phi_eval"], t_ref), c["label"], case.d_presc, t_ref, case.n_iso)
     cs = make(lgk, case, 2, rho_adapt=1)
-    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=TOL, max_iter=20000)
+    res = lgk.solve_weightings(cs, c["W"], c["rho"], tol=SOLVE_TOL, max_iter=20000)
     st = lgk.fetch_stats(res)
     assert st["converged"].all()
     gap = np.abs(st["obj"] - c["opt"]) / np.maximum(1.0, np.abs(c["opt"]))
@@ -469,7 +479,7 @@ def test_adaptive_rho_converged_parity(lgk, cfg0):
     for key in ("coverage", "selectivity", "gi", "bot"):
         rel = np.abs(met[key] - met_ref[key]) / np.abs(met_ref[key])
         assert rel.max() <= 5e-3, (key, rel)
-    fixed = lgk.fetch_stats(lgk.solve_weightings(make(lgk, case, 2), c["W"], c["rho"], tol=TOL,
+    fixed = lgk.fetch_stats(lgk.solve_weightings(make(lgk, case, 2), c["W"], c["rho"], tol=SOLVE_TOL,
                                                  max_iter=20000))
     assert st["iters"].mean() <= fixed["iters"].mean(), (st["iters"], fixed["iters"])
 
@@ -479,10 +489,9 @@ def test_tensor_core_schur_complement_matches_fp64(lgk, cfg0, prec):
     """S = I + A A^T formed on the tensor cores (exact BF16 products, FP32
     sums of 128-column chunks, FP64 across chunks; the default) against the
     FP64 product on the CUDA cores (setup_fp64 = 1, exact from the rounded
-    A).  One iteration from the same state: S enters only through S^{-1}, and
-    an entrywise error of ~1e-6 relative in S moves v by ~1e-6 of v, so the
-    two states agree to 1e-5 of their largest entry; and both agree with the
-    oracle within the one-step bound."""
+    A).  One iteration from the same state: S enters only through S^{-1}, so
+    the two states agree to ||A||_2^2 2^-19 of their largest entry; and both
+    agree with the oracle within the one-step bound."""
     c = cfg0
     A = lp_matrix(c["lp"], lgk, prec)
     ok = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=300)
@@ -494,11 +503,42 @@ def test_tensor_core_schur_complement_matches_fp64(lgk, cfg0, prec):
         out.append(lgk.fetch_state(res))
         cs.close()
     (a1, a2), (b1, b2) = out
-    assert np.abs(a1 - b1).max() <= 1e-5 * np.abs(b1).max()
-    assert np.abs(a2 - b2).max() <= 1e-5 * np.abs(b2).max()
+    # each entry of S carries at most 24 FP32 accumulation steps (2 k blocks
+    # x 3 products x 4 MMAs) of 2^-24 relative rounding, ~2^-19.4, which reach
+    # the state amplified by at most ||A||_2^2 (as in the one-step bound)
+    sb = np.linalg.norm(A, 2) ** 2 * 2.0 ** -19
+    assert np.abs(a1 - b1).max() <= sb * np.abs(b1).max()
+    assert np.abs(a2 - b2).max() <= sb * np.abs(b2).max()
     o = AD.admm(A, c["lp"].c, c["b"], c["l"], c["u"], c["rho"], max_iter=1,
                 state=(ok.z1, ok.z2, ok.y1, ok.y2))
     r1, r2 = o.z1 + o.y1, o.z2 + o.y2
     tol = np.linalg.norm(A, 2) ** 2 * unit_roundoff(lgk, prec, A.shape[1])
     assert np.abs(a1.T - r1).max() <= tol * np.abs(r1).max()
     assert np.abs(a2.T - r2).max() <= tol * np.abs(r2).max()
+
+
+def test_autotuned_solve(lgk, cfg0):
+    """lgk_params.autotune: the first solve of a case at 32 columns (lagged
+    two-term form) times each GEMM configuration on one replay of the real
+    iteration (256- or 128-row tiles for the A GEMMs x the solve's column
+    tile whole or halved) and keeps the fastest for the case.  Later solves
+    at that width start with it: two of them agree bit for bit.  The tuned
+    plans meet the same converged gates as untuned ones (objective within
+    1e-3 of the untuned solve's, which the other tests hold to the simplex)."""
+    c = cfg0
+    lp = c["lp"]
+    W = SC.slider_weights(6)[:32]
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    cs = make(lgk, c["case"], 2, autotune=1)
+    first = lgk.fetch_stats(lgk.solve_weightings(cs, W, rho, tol=SOLVE_TOL, max_iter=20000))
+    a = lgk.solve_weightings(cs, W, rho, tol=SOLVE_TOL, max_iter=20000)
+    b = lgk.solve_weightings(cs, W, rho, tol=SOLVE_TOL, max_iter=20000)
+    sa, sb = lgk.fetch_stats(a), lgk.fetch_stats(b)
+    np.testing.assert_array_equal(sa["obj"], sb["obj"])
+    np.testing.assert_array_equal(lgk.fetch_state(a)[0], lgk.fetch_state(b)[0])
+    plain = lgk.fetch_stats(lgk.solve_weightings(make(lgk, c["case"], 2), W, rho, tol=SOLVE_TOL,
+                                                 max_iter=20000))
+    for st in (first, sa):
+        assert st["converged"].all()
+        gap = np.abs(st["obj"] - plain["obj"]) / np.maximum(1.0, np.abs(plain["obj"]))
+        assert gap.max() <= 1e-3, gap

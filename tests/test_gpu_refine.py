@@ -98,14 +98,14 @@ def test_converged_parity_with_refinement(lgk):
     rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
     opt = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(W.shape[0])])
     cs = make(lgk, case, solve_refine=1)
-    res = lgk.solve_weightings(cs, W, rho, tol=1e-4, max_iter=20000)
+    res = lgk.solve_weightings(cs, W, rho, tol=5e-5, max_iter=20000)     # 1e-3 objective bar headroom
     st = lgk.fetch_stats(res)
     assert st["converged"].all()
     gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
     assert gap.max() <= 1e-3, gap
     assert st["rel_pri"].max() <= 1e-4 and st["rel_dual"].max() <= 1e-4
     ck = lgk.fetch_check(res)
-    assert np.all(np.abs(ck["gap"]) <= 1e-3) and np.all(ck["infeas"] <= 1e-4)
+    assert np.all(ck["primal"] <= 1e-4), ck["primal"]    # refined: within tol itself
     # the profile shows the refinement's launches: 2 solves per iteration
     cs_p = make(lgk, case, solve_refine=1, profile=1)
     p = lgk.fetch_profile(lgk.solve_weightings(cs_p, W, rho, tol=0.0, max_iter=20))
