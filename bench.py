@@ -772,6 +772,9 @@ def serve_cases(n_req, seed=4000):
     return out
 
 
+_SERVE_CACHE = {}
+
+
 def serve_run(lgk, args, local, n_cases, rate, workers, width=32, seed=4000):
     """One Poisson stream of serving requests through lgk_server (continuous
     batching): every case is opened as a resident case with its initial
@@ -781,7 +784,10 @@ def serve_run(lgk, args, local, n_cases, rate, workers, width=32, seed=4000):
     throughput and latency figures."""
     import threading
     from synth import cases as SC
-    reqs = serve_cases(n_cases + 3, seed=seed)
+    key = (n_cases, seed)
+    if key not in _SERVE_CACHE:                 # the same workload at every rate of a sweep
+        _SERVE_CACHE[key] = serve_cases(n_cases + 3, seed=seed)
+    reqs = _SERVE_CACHE[key]
     warm, reqs = reqs[:3], reqs[3:]
     srv = lgk.Server(workers=workers, tol=args.tol, max_iter=args.max_iter, w0_bot=SC.W0_BOT,
                      rho0_per_beta=RHO0_PER_BETA, stream_width=width,
