@@ -168,7 +168,11 @@ int lgk_default_params(lgk_params* p);
  *
  * desc, p: host structs (p may be NULL for defaults).  *out receives the case.
  * Errors: LGK_EINVAL (bad sizes/classes/NaN), LGK_EBUDGET, LGK_ENOMEM,
- * LGK_ENOTPD, LGK_ECUDA.  On error *out is set to NULL.
+ * LGK_ENOTPD, LGK_ECUDA.  On error *out is set to NULL.  The scalar fields
+ * and the point classes are checked on the host before any CUDA call; the
+ * dose rates phi (n_pts x 24 n_iso, up to GBs) are checked on the device as
+ * A is assembled from them: a NaN, infinite or negative entry also returns
+ * LGK_EINVAL, after the copy to the device.
  */
 int lgk_create_case(const lgk_case_desc* desc, const lgk_params* p, lgk_case** out);
 

@@ -103,11 +103,24 @@ __host__ __device__ inline int n_slots(int n_targets) { return 3 * n_targets + 5
 constexpr int kMaxTargets = 64;      // keeps slot ids below 255
 
 // Exact round-to-nearest-even of an FP64 value to bfloat16 (8 significant
-// bits, FP32 exponent range, subnormal spacing 2^-133): scale to an integer
-// significand, round with rint (ties to even), scale back.  The result has at
-// most 8 significant bits and lies in float range, so the float conversion and
-// the final bf16 conversion are exact.
+// bits, FP32 exponent range, subnormal spacing 2^-133).  Normal range
+// (|x| >= 2^-126): round the 52-bit fraction to its top 7 bits on the bit
+// pattern (add half an ulp minus one, plus the kept lsb, then clear the 45
+// dropped bits; a carry moves into the exponent correctly).  Below 2^-126:
+// scale to an integer significand, round with rint (ties to even), scale
+// back.  Either result has at most 8 significant bits and lies in float
+// range (or overflows to inf), so the float and bf16 conversions are exact.
 __device__ inline __nv_bfloat16 bf16_from_double(double x) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int bexp = (int)((bits >> 52) & 0x7ff);
+    if (bexp != 0x7ff && bexp >= 1023 - 126) {
+        bits += 0x00000FFFFFFFFFFFull + ((bits >> 45) & 1ull);
+        bits &= ~0x00001FFFFFFFFFFFull;
+        const double r = __longlong_as_double((long long)bits);
+        const float rf = fabs(r) >= 0x1p128 ? (r < 0 ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000))
+                                            : (float)r;
+        return __float2bfloat16_rn(rf);
+    }
     if (x == 0.0 || !isfinite(x)) return __float2bfloat16_rn((float)x);
     double ax = fabs(x);
     int e;

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <string>
 #include <vector>
 
@@ -34,13 +35,20 @@ size_t CaseData::bytes_held() const {
 // ------------------------------------------------------------- assembly
 
 // A[b][p] = sign_p phi[p][b] / D_p for point columns (32x32 tiled transpose).
+// phi is validated here, on its one pass through the device: an entry that is
+// negative, infinite or NaN sets *bad.
 __global__ void k_assemble_points(const double* __restrict__ phi, const double* __restrict__ scale,
-                                  int P, int B, double* __restrict__ A, int lda) {
+                                  int P, int B, double* __restrict__ A, int lda, int* bad) {
     __shared__ double tile[32][33];
     int p0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
         int p = p0 + k, b = b0 + threadIdx.x;
-        tile[k][threadIdx.x] = (p < P && b < B) ? phi[(size_t)p * B + b] * scale[p] : 0.0;
+        double v = 0.0;
+        if (p < P && b < B) {
+            v = phi[(size_t)p * B + b];
+            if (!(v >= 0.0 && v <= DBL_MAX)) atomicExch(bad, 1);
+        }
+        tile[k][threadIdx.x] = v * (p < P ? scale[p] : 0.0);
     }
     __syncthreads();
     for (int k = threadIdx.y; k < 32; k += 8) {
@@ -85,11 +93,12 @@ __global__ void k_row_norm(const double* __restrict__ A, int lda, int ncols, int
 // A = hi + lo holds exactly in FP64.
 template <int NA>
 __global__ void k_scale_round(double* __restrict__ A64, const double* __restrict__ Dr, int m_pad,
-                              int n_pad, int P, int n, double beta, void* __restrict__ out) {
-    size_t total = (size_t)m_pad * n_pad;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        int i = (int)(e / n_pad), p = (int)(e % n_pad);
+                              int n_pad, int P, int n, double beta, void* __restrict__ out, int keep) {
+    const size_t total = (size_t)m_pad * n_pad;
+    // rows over blockIdx.y (grid-stride), columns over x: no 64-bit division
+    for (int i = blockIdx.y; i < m_pad; i += gridDim.y)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += gridDim.x * blockDim.x) {
+        const size_t e = (size_t)i * n_pad + p;
         double a = A64[e] * Dr[i];
         if (p >= P && p < n) a *= beta;
         if (NA > 0) {
@@ -102,11 +111,11 @@ __global__ void k_scale_round(double* __restrict__ A64, const double* __restrict
                 o[total + e] = l;
                 kept += (double)__bfloat162float(l);
             }
-            A64[e] = kept;
+            if (keep) A64[e] = kept;
         } else {
             float f = (float)a;
             static_cast<float*>(out)[e] = f;
-            A64[e] = (double)f;
+            if (keep) A64[e] = (double)f;
         }
     }
 }
@@ -114,7 +123,10 @@ __global__ void k_scale_round(double* __restrict__ A64, const double* __restrict
 // ---------------------------------------------------------------- FP64 GEMM
 // C[M x N] = alpha op(A) op(B) + beta C; op(A) M x K (TA: A stored K x M),
 // op(B) K x N (TB: B stored N x K).  LOWER skips tiles above the diagonal.
-template <bool TA, bool TB, bool LOWER>
+// TRI (C = Y^T Y with Y lower triangular, stored K x M and K x N): the terms
+// k < max(row, column) are zero, so a tile's k range starts at the larger of
+// its first row and column.
+template <bool TA, bool TB, bool LOWER, bool TRI = false>
 __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha,
                                                const double* __restrict__ A, int lda,
                                                const double* __restrict__ B, int ldb,
@@ -130,7 +142,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, double alpha
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = TRI ? max(m0, n0) : 0; k0 < K; k0 += 16) {
         for (int e = threadIdx.x; e < 1024; e += 256) {
             int mm, kk;
             if (TA) { kk = e >> 6; mm = e & 63; } else { mm = e >> 4; kk = e & 15; }
@@ -510,13 +522,21 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
     {
         dim3 grid((P + 31) / 32, (B + 31) / 32), blk(32, 8);
         k_assemble_points<<<grid, blk, 0, st>>>(phi_d.as<double>(), scale_d.as<double>(), P, B,
-                                                A64.as<double>(), n_pad);
+                                                A64.as<double>(), n_pad, cs.ctrl_setup.as<int>() + 1);
         LGK_LAUNCH_CHECK();
         k_assemble_bot<<<(8 * N + 255) / 256, 256, 0, st>>>(P, N, B, d.phi_cal / d_mean,
                                                             A64.as<double>(), n_pad);
         LGK_LAUNCH_CHECK();
     }
-    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+        int bad = 0;
+        LGK_CUDA_TRY(cudaMemcpyAsync(&bad, cs.ctrl_setup.as<int>() + 1, 4, cudaMemcpyDeviceToHost, st));
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        if (bad) {
+            set_error("phi must be finite and >= 0");
+            return LGK_EINVAL;
+        }
+    }
     phi_d.alloc(0);
     scale_d.alloc(0);
 
@@ -529,27 +549,31 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
         LGK_CUDA_TRY(cudaMemcpyAsync(cs.Dr.p, ones.data(), (size_t)m_pad * 8, cudaMemcpyHostToDevice, st));
         LGK_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    if (cs.na == 2) {
-        if ((rc = cs.Ahat.alloc((size_t)2 * m_pad * n_pad * 2))) return rc;
-        k_scale_round<2><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
-                                                  P, n, cs.beta, cs.Ahat.p);
-    } else if (cs.na == 1) {
-        if ((rc = cs.Ahat.alloc((size_t)m_pad * n_pad * 2))) return rc;
-        k_scale_round<1><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
-                                                  P, n, cs.beta, cs.Ahat.p);
-    } else {
-        if ((rc = cs.A32.alloc((size_t)m_pad * n_pad * 4))) return rc;
-        k_scale_round<0><<<148 * 8, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad,
-                                                  P, n, cs.beta, cs.A32.p);
-    }
-    LGK_LAUNCH_CHECK();
-
     // ---- S = A A^T + I from exactly the rounded A, Cholesky, inverse.  BF16
     // forms: on the tensor cores from the BF16 terms (exact products, FP32
     // sums of short chunks, FP64 across chunks); FP32 form, or setup_fp64:
-    // FP64 products on the CUDA cores.
+    // FP64 products on the CUDA cores (from the FP64 copy of the rounded A,
+    // which only then is written back).
     DevBuf S, Y;
     const bool tc_s = bf16 && !cs.prm.setup_fp64;
+    {
+        const dim3 grid(8, (unsigned)std::min(m_pad, 4096));
+        const int keep = tc_s ? 0 : 1;
+        if (cs.na == 2) {
+            if ((rc = cs.Ahat.alloc((size_t)2 * m_pad * n_pad * 2))) return rc;
+            k_scale_round<2><<<grid, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad, P, n,
+                                                   cs.beta, cs.Ahat.p, keep);
+        } else if (cs.na == 1) {
+            if ((rc = cs.Ahat.alloc((size_t)m_pad * n_pad * 2))) return rc;
+            k_scale_round<1><<<grid, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad, P, n,
+                                                   cs.beta, cs.Ahat.p, keep);
+        } else {
+            if ((rc = cs.A32.alloc((size_t)m_pad * n_pad * 4))) return rc;
+            k_scale_round<0><<<grid, 256, 0, st>>>(A64.as<double>(), cs.Dr.as<double>(), m_pad, n_pad, P, n,
+                                                   cs.beta, cs.A32.p, keep);
+        }
+        LGK_LAUNCH_CHECK();
+    }
     if (tc_s) {
         LGK_CUDA_TRY(cudaStreamSynchronize(st));
         A64.alloc(0);               // the BF16 terms are all the tensor cores need
@@ -625,9 +649,18 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
                 return rc;
         }
     }
-    // S^{-1} = L^{-T} L^{-1} = Y^T Y (reuse the S buffer)
-    if ((rc = dgemm(st, true, false, m_pad, m_pad, m_pad, 1.0, Yd, m_pad, Yd, m_pad, 0.0, Sd, m_pad)))
-        return rc;
+    // S^{-1} = L^{-T} L^{-1} = Y^T Y (reuse the S buffer): the lower tiles,
+    // each over its k range (Y lower triangular: a sixth of the full
+    // product's flops), then the upper triangle mirrored from the lower
+    {
+        dim3 grid((m_pad + 63) / 64, (m_pad + 63) / 64);
+        k_dgemm<true, false, true, true><<<grid, 256, 0, st>>>(m_pad, m_pad, m_pad, 1.0, Yd, m_pad, Yd, m_pad,
+                                                               0.0, Sd, m_pad);
+        LGK_LAUNCH_CHECK();
+        dim3 gt((m_pad + 31) / 32, (m_pad + 31) / 32), bt(32, 8);
+        k_mirror_lower<<<gt, bt, 0, st>>>(Sd, m_pad, m_pad);
+        LGK_LAUNCH_CHECK();
+    }
     size_t mm = (size_t)m_pad * m_pad;
     if (bf16) {
         if ((rc = cs.G3.alloc(mm * 3 * 2))) return rc;

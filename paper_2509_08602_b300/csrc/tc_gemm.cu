@@ -185,6 +185,34 @@ __device__ inline void epi_resid(float res[kChunk][5], float* red, double* dst, 
     epi_bar();
 }
 
+// The A tiles of one stage (k block kx, output rows row0 ..): NA terms x MT
+// sub-tiles of 128 rows; an MN-major tile is two 64-row boxes.
+template <int NA, int NT, bool A_MN, int EPI, int MT>
+__device__ inline void load_a_stage(const CUtensorMap* tmA, uint32_t st, uint32_t full, int row0, int kx,
+                                    uint64_t pol_a) {
+    if (A_MN) {
+#pragma unroll
+        for (int p = 0; p < NA; ++p)
+#pragma unroll
+            for (int h = 0; h < MT; ++h) {
+                const uint32_t dst = st + (p * MT + h) * kABytes;
+                tma_load_3d_hint(dst, tmA, row0 + h * 128, kx, p, full, pol_a);
+                tma_load_3d_hint(dst + kABytes / 2, tmA, row0 + h * 128 + 64, kx, p, full, pol_a);
+            }
+    } else if (EPI == EPI_PARTIAL && NT == 6) {
+        // the solve: S^{-1} is re-read every iteration, default policy
+        // (an evict-last hint did not keep its 6 m^2 bytes in L2)
+#pragma unroll
+        for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, tmA, kx, row0, p, full);
+    } else {
+#pragma unroll
+        for (int p = 0; p < NA; ++p)
+#pragma unroll
+            for (int h = 0; h < MT; ++h)
+                tma_load_3d_hint(st + (p * MT + h) * kABytes, tmA, kx, row0 + h * 128, p, full, pol_a);
+    }
+}
+
 // MT: 128-row sub-tiles per output tile.  MT = 2 puts two accumulators side by
 // side (256 rows) on one B tile: half the B traffic per A byte, and twice the
 // A bytes per pipeline stage, so more of A is in flight per SM (the one-term-A
@@ -221,12 +249,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // The A operand (the case matrix's BF16 terms, or S^{-1}) is written at
+    // set-up and by no kernel of the iteration, so the first stages' A tiles
+    // are loaded before the wait on the previous kernel and arrive during its
+    // tail.  Their bytes are added to the stage's full barrier as a pending
+    // transaction without an arrival: the stage cannot complete before the
+    // arrival that comes with its B tile, after the wait.  (Not for launches
+    // that work only in the solve's first iteration: they mostly do nothing.)
+    const uint32_t a_bytes = (uint32_t)(NA * MT * kABytes);
+    int pre = 0;
+    if (!a.first_only && warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+        const uint64_t pol_a = policy_evict_first();
+        for (int sg = s0; sg < s1 && pre < S; ++sg) {
+            const int* g = a.seg + 5 * sg;
+            for (int kb = g[2]; kb < g[3] && pre < S; ++kb, ++pre) {
+                const uint32_t full = smem_u32(&bars[pre]);
+                mbar_expect_tx_only(full, a_bytes);
+                load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, smem_u32(smem + (size_t)pre * a.stage_bytes), full,
+                                                    g[0] * 128 * MT, kb * 64, pol_a);
+            }
+        }
+    }
     // set-up done; from here on the previous kernel's output is read
     pdl_wait();
     const bool run = ctrl->n_active != 0 && ctrl->err == 0 && (!a.first_only || ctrl->iter == 0);
 
     if (!run) {
         // every column has stopped (or an error is pending): nothing to do
+        // but let the prefetched A tiles land (bounded) before the CTA exits
+        if (warp == 0 && lane == 0)
+            for (int s = 0; s < pre; ++s) {
+                mbar_arrive(smem_u32(&bars[s]));
+                mbar_wait(smem_u32(&bars[s]), 0u, err);
+            }
     } else if (warp == 0 && lane == 0) {
         // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
@@ -240,35 +297,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = g[2]; kb < g[3] && ok; ++kb, ++it) {
                 const int s = it % S;
                 const uint32_t ph = (uint32_t)(it / S) & 1u;
-                ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
-                if (!ok) break;
                 const uint32_t full = smem_u32(&bars[s]);
                 const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-                mbar_expect_tx(full, (uint32_t)a.stage_bytes);
                 const int kx = kb * 64;
-                if (A_MN) {
-#pragma unroll
-                    for (int p = 0; p < NA; ++p)
-#pragma unroll
-                        for (int h = 0; h < MT; ++h) {
-                            const uint32_t dst = st + (p * MT + h) * kABytes;
-                            tma_load_3d_hint(dst, &tmA, row0 + h * 128, kx, p, full, pol_a);
-                            tma_load_3d_hint(dst + kABytes / 2, &tmA, row0 + h * 128 + 64, kx, p, full, pol_a);
-                        }
-                } else if (EPI == EPI_PARTIAL && NT == 6) {
-                    // the solve: S^{-1} is re-read every iteration, default policy
-                    // (an evict-last hint did not keep its 6 m^2 bytes in L2)
-#pragma unroll
-                    for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, &tmA, kx, row0, p, full);
+                if (it < pre) {
+                    // A already in flight (prefetched): the arrival and the B bytes
+                    mbar_expect_tx(full, (uint32_t)a.stage_bytes - a_bytes);
                 } else {
-#pragma unroll
-                    for (int p = 0; p < NA; ++p)
-#pragma unroll
-                        for (int h = 0; h < MT; ++h)
-                            tma_load_3d_hint(st + (p * MT + h) * kABytes, &tmA, kx, row0 + h * 128, p, full,
-                                             pol_a);
+                    ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
+                    if (!ok) break;
+                    mbar_expect_tx(full, (uint32_t)a.stage_bytes);
+                    load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, st, full, row0, kx, pol_a);
                 }
-                const uint32_t sb = st + NA * MT * kABytes;
+                const uint32_t sb = st + a_bytes;
 #pragma unroll
                 for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &tmB, kx, col0, p, full);
             }

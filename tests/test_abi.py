@@ -1,6 +1,7 @@
 """CPU checks of the C ABI: the library loads, exports every entry point the
 header declares, and rejects invalid arguments on the host (no GPU needed:
-argument checking happens before any CUDA call)."""
+argument checking happens before any CUDA call), except the dose-rate
+matrix, whose values the assembly kernel checks (one GPU test)."""
 import ctypes
 import os
 import re
@@ -46,12 +47,28 @@ def _tiny(nan=False, bad_kind=False, bad_target=False):
     return phi, kind, sid
 
 
-@pytest.mark.parametrize("kw", [dict(nan=True), dict(bad_kind=True), dict(bad_target=True)])
+@pytest.mark.parametrize("kw", [dict(bad_kind=True), dict(bad_target=True)])
 def test_create_case_rejects_bad_inputs(lgk, kw):
     phi, kind, sid = _tiny(**kw)
     with pytest.raises(lgk.LgkError) as e:
         lgk.create_case(phi, kind, sid, 1, [20.0], [1.0], [1.0], 10.0, 5.0, 3.0)
     assert e.value.code == 1
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -1e-3])
+def test_create_case_rejects_bad_phi_on_the_device(lgk, bad):
+    """phi (up to GBs) is validated by the assembly kernel, not by a host
+    scan: a NaN, infinite or negative dose rate still gives LGK_EINVAL."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    phi, kind, sid = _tiny()
+    phi[2, 17] = bad
+    with pytest.raises(lgk.LgkError) as e:
+        lgk.create_case(phi, kind, sid, 1, [20.0], [1.0], [1.0], 10.0, 5.0, 3.0)
+    assert e.value.code == 1 and "phi" in str(e.value)
+    lgk.create_case(*_tiny()[:3], 1, [20.0], [1.0], [1.0], 10.0, 5.0, 3.0).close()
 
 
 def test_create_case_rejects_bad_thresholds(lgk):
