@@ -123,7 +123,7 @@ typedef struct {
                                 the reported plans use the column's current rho.
                                 0 (default): rho fixed per column (Eq. rho_rule or caller's). */
     int solve_refine;        /* BF16 forms: iterative refinement steps of the x-update's solve
-                                per iteration, 0..2 (default 0).  v = S^{-1} rhs is a product
+                                per iteration, 0..2 (default 0; see also refine_after).  v = S^{-1} rhs is a product
                                 with the explicit inverse whose FP32 sums lose accuracy when
                                 rhs is large along the directions S magnifies (v is then
                                 ~1000x smaller than rhs); each step computes the residual
@@ -148,6 +148,15 @@ typedef struct {
                                 solves of that case and count.  The configurations sum in
                                 different orders, so plans then differ in rounding from an
                                 untuned solve.  0 (default): the fixed rule.                 */
+    int refine_after;        /* BF16 forms with solve_refine = 0: once a solve has run this many
+                                iterations with columns still active (a stream: once its
+                                oldest running column has), it continues with one refinement
+                                step per iteration (as solve_refine = 1), for every column,
+                                to the end of the solve.  Columns whose residuals level off
+                                above tol (the explicit-inverse solve's accuracy floor, near
+                                5e-5 on the 5000 x 61600 case) then converge.  Needs S's three
+                                BF16 terms (6 m^2 device bytes, kept whenever this is > 0).
+                                0 = never.  Default 4000.                                    */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */

@@ -857,23 +857,31 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
 
     // capture a CUDA graph of `per_graph` iterations, replay until done
     cudaGraph_t g = nullptr;
-    // kernel classes of one iteration, in launch order
-    if (bf16) {
-        r.prof_class = {LGK_K_GEMM1_LO, LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE};
-        for (int step = 0; step < r.refine_steps; ++step)
-            r.prof_class.insert(r.prof_class.end(),
-                                {LGK_K_SV, LGK_K_REDUCE_ERR, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE});
-        r.prof_class.insert(r.prof_class.end(), {LGK_K_GEMM2_LO, LGK_K_GEMM2, LGK_K_FINALIZE});
-    }
-    else
-        r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
-                        LGK_K_GEMM2, LGK_K_Q1_UPDATE, LGK_K_FINALIZE};
-    const size_t kpi = r.prof_class.size();
-    if (cs.prm.profile) {
-        r.prof_ev.assign((size_t)per_graph * (kpi + 1), nullptr);
-        for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
-        r.prof_ran.assign((size_t)per_graph * kpi, 1);
-    }
+    // kernel classes of one iteration, in launch order (again when the
+    // iteration changes form: refine_after)
+    size_t kpi = 0;
+    auto prof_init = [&]() -> int {
+        if (bf16) {
+            r.prof_class = {LGK_K_GEMM1_LO, LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE};
+            for (int step = 0; step < r.refine_steps; ++step)
+                r.prof_class.insert(r.prof_class.end(),
+                                    {LGK_K_SV, LGK_K_REDUCE_ERR, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE});
+            r.prof_class.insert(r.prof_class.end(), {LGK_K_GEMM2_LO, LGK_K_GEMM2, LGK_K_FINALIZE});
+        } else {
+            r.prof_class = {LGK_K_GEMM1, LGK_K_REDUCE_RHS, LGK_K_SOLVE, LGK_K_REDUCE_SOLVE,
+                            LGK_K_GEMM2, LGK_K_Q1_UPDATE, LGK_K_FINALIZE};
+        }
+        kpi = r.prof_class.size();
+        if (cs.prm.profile) {
+            for (cudaEvent_t e : r.prof_ev)
+                if (e) cudaEventDestroy(e);
+            r.prof_ev.assign((size_t)per_graph * (kpi + 1), nullptr);
+            for (auto& e : r.prof_ev) LGK_CUDA_TRY(cudaEventCreate(&e));
+            r.prof_ran.assign((size_t)per_graph * kpi, 1);
+        }
+        return LGK_OK;
+    };
+    if ((rc = prof_init())) return rc;
     size_t n_nodes = 0;
     // capture the graph of `per_graph` iterations with the current ctx
     auto capture = [&]() -> int {
@@ -1269,6 +1277,20 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             cudaGraphExecDestroy(r.graph);
             r.graph = nullptr;
             r.refine = false;
+            if ((rc = tc_prepare(r))) break;
+            cx = make_ctx(r);
+            if ((rc = capture())) break;
+        }
+        if (bf16 && r.refine_steps == 0 && cs.S3.p && cs.prm.refine_after > 0 && age >= cs.prm.refine_after) {
+            // columns still running this long: continue with one refinement
+            // step of the solve per iteration (their residuals may have
+            // levelled off at the unrefined solve's accuracy floor)
+            cudaGraphExecDestroy(r.graph);
+            r.graph = nullptr;
+            const size_t mq2 = (size_t)Kp * cs.m_pad;
+            if ((rc = r.rhs32.alloc(mq2 * 4)) || (rc = r.rv.alloc(mq2 * 4)) || (rc = r.V3.alloc(mq2 * 6))) break;
+            r.refine_steps = 1;
+            if ((rc = prof_init())) break;
             if ((rc = tc_prepare(r))) break;
             cx = make_ctx(r);
             if ((rc = capture())) break;

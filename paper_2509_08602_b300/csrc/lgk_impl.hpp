@@ -31,6 +31,10 @@ struct DevBuf {
 
 struct CheckTC;   // tensor-core plan check of a case (check.cu)
 
+// S's three BF16 terms are kept when a solve may refine its x-update: from
+// its start (solve_refine) or after refine_after iterations.
+inline bool keeps_s3(const lgk_params& p) { return p.solve_refine > 0 || p.refine_after > 0; }
+
 struct CaseData {
     lgk_params prm{};
     int device = 0;
@@ -57,7 +61,7 @@ struct CaseData {
     int na = 0;        // BF16 terms of A: 1 (LGK_PREC_BF16), 2 (LGK_PREC_BF16X3)
     DevBuf G32;        // float [m_pad][m_pad] S^{-1}    (LGK_PREC_FP32)
     DevBuf G3;         // bf16 [3][m_pad][m_pad] S^{-1} = hi + mid + lo (BF16 forms)
-    DevBuf S3;         // bf16 [3][m_pad][m_pad] S = hi + mid + lo (BF16 forms, solve_refine > 0)
+    DevBuf S3;         // bf16 [3][m_pad][m_pad] S = hi + mid + lo (BF16 forms, keeps_s3)
     DevBuf ctrl_setup; // int [4] device error flags during set-up
     std::atomic<int> async_busy{0};   // an asynchronous solve of this case is running
     std::unique_ptr<CheckTC> chk_tc;  // plans, maps and buffers of the plan check, made on first use

@@ -455,7 +455,7 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
     // resident footprint check before any large allocation
     size_t resident = (size_t)n_pad + (size_t)m_pad * 8 + 64 +
                       (bf16 ? (size_t)cs.na * m_pad * n_pad * 2 +
-                                  (size_t)(cs.prm.solve_refine > 0 ? 6 : 3) * m_pad * m_pad * 2
+                                  (size_t)(keeps_s3(cs.prm) ? 6 : 3) * m_pad * m_pad * 2
                             : (size_t)m_pad * n_pad * 4 + (size_t)m_pad * m_pad * 4);
     if (cs.prm.hbm_budget && resident > cs.prm.hbm_budget) {
         set_error("case footprint " + std::to_string(resident) + " B exceeds hbm_budget " +
@@ -601,7 +601,7 @@ int setup_case(CaseData& cs, const lgk_case_desc& d) {
         LGK_LAUNCH_CHECK();
         if ((rc = a_norm_estimate(st, S.as<double>(), m_pad, m_pad, &cs.a_norm))) return rc;
     }
-    if (bf16 && cs.prm.solve_refine > 0) {     // S itself, for the refinement's residual rhs - S v
+    if (bf16 && keeps_s3(cs.prm)) {     // S itself, for the refinement's residual rhs - S v
         if ((rc = cs.S3.alloc((size_t)m_pad * m_pad * 3 * 2))) return rc;
         k_split3_sym<<<148 * 8, 256, 0, st>>>(S.as<double>(), m_pad, m_pad, cs.S3.as<__nv_bfloat16>());
         LGK_LAUNCH_CHECK();

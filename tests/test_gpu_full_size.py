@@ -6,10 +6,16 @@ times, against stored oracle plans:
   * the 5000 x 61600 four-target case (200 isocenters, 60000 points): its 441
     weightings streamed through 128 columns;
 
-BF16X3 form with the lagged low term, solved to relative residual 5e-5 (the
-the benchmark spec gates are residuals <= 1e-4 and objective within 1e-3; a stop at
-1e-4 leaves the objective about 1e-3 from the optimum, so the tests stop at
-5e-5 for headroom).
+BF16X3 form with the lagged low term and one refinement step of the
+x-update's solve per iteration (lgk_params.solve_refine = 1), solved to
+relative residual 5e-5.  The gates are the oracle's: objective within 1e-3,
+residuals <= 1e-4, plan metrics within 0.5 %.  Two plans that each pass a
+residual test at 1e-4 can be several 1e-3 apart in objective on these
+degenerate LPs (the unrefined solve at 1e-4 measured up to 7e-3 on the
+5000 x 61600 case against the oracle at 5e-5), so both sides stop at 5e-5;
+without refinement the explicit-inverse solve levels the residuals off near
+5e-5 on that case (27 of 441 weightings reached the stop in 20000
+iterations), with it all converge.
 
 The stored plans (tests/golden/full_size_cfg{1,2}.json, written by
 tests/golden/make_full_size.py, which calls only the oracle) are the FP64
@@ -70,7 +76,8 @@ def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width):
     order = np.argsort(W_all[:, 3], kind="stable")         # lowest BOT weight first
     W = W_all[order]
     cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc,
-                         case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal)
+                         case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                         params=lgk.default_params(solve_refine=1))
     assert (cs.m, cs.n) == (gold["m"], gold["n"])
     s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=gold["rho0"], tol=SOLVE_TOL, max_iter=20000,
                          width=width, check=True)
@@ -97,6 +104,12 @@ def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width):
         met = M.plan_metrics(M.dose(phi_eval, t), label, case.d_presc, t, case.n_iso)
         rel = {key: abs(met[key][0] - g[key]) / abs(g[key])
                for key in ("coverage", "selectivity", "gi", "bot") if g[key] is not None}
-        rows.append((g["index"], gap, rel))
-    assert all(gap <= 1e-3 for _, gap, _ in rows), rows
-    assert all(max(rel.values()) <= 5e-3 for _, _, rel in rows), rows
+        rows.append((g["index"], gap, rel, int(s["iters"][k]), g["iters"]))
+    # the per-plan error table against the FP64 oracle (pytest -s prints it)
+    table = "\n".join(
+        f"  grid {i:4d}  iters {it_d:5d} (oracle {it_o:5d})  obj {gap:.2e}  "
+        + "  ".join(f"{key} {v:.2e}" for key, v in rel.items())
+        for i, gap, rel, it_d, it_o in rows)
+    print(f"\n{gold['m']} x {gold['n']}, width {width}: relative errors against the FP64 oracle\n{table}")
+    assert all(gap <= 1e-3 for _, gap, _, _, _ in rows), table
+    assert all(max(rel.values()) <= 5e-3 for _, _, rel, _, _ in rows), table

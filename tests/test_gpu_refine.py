@@ -110,3 +110,32 @@ def test_converged_parity_with_refinement(lgk):
     cs_p = make(lgk, case, solve_refine=1, profile=1)
     p = lgk.fetch_profile(lgk.solve_weightings(cs_p, W, rho, tol=0.0, max_iter=20))
     assert p["solve"][1] == 40 and p["sv"][1] == 20 and p["reduce_err"][1] == 20
+
+
+def test_refinement_switched_on_mid_solve(lgk):
+    """refine_after: a solve still running after that many iterations
+    continues with one refinement step per iteration (re-captured graph, same
+    state); the plans meet the gates of the refined solve, and the profile
+    counts the refinement's launches only after the switch."""
+    case = SC.workload_case(0)
+    lp = L.precondition(L.assemble_case(case))
+    W = SC.slider_weights(3)
+    b, l, u = L.bounds(lp, W)
+    rho = L.rho_rule(W[:, 3], SC.W0_BOT, L.rho0_for(lp))
+    opt = np.array([SX.simplex(lp.A, b[:, j], lp.c, u[:, j]).obj for j in range(W.shape[0])])
+    cs = make(lgk, case, refine_after=200, profile=1)
+    res = lgk.solve_weightings(cs, W, rho, tol=5e-5, max_iter=20000)
+    st = lgk.fetch_stats(res)
+    assert st["converged"].all() and st["iters"].max() > 250
+    gap = np.abs(st["obj"] - opt) / np.maximum(1.0, np.abs(opt))
+    assert gap.max() <= 1e-3, gap
+    assert np.all(lgk.fetch_check(res)["primal"] <= 1e-4)
+    p = lgk.fetch_profile(res)
+    n_it = p["gemm1"][1]
+    assert n_it == st["iters"].max()
+    assert p["sv"][1] == n_it - 200 and p["reduce_err"][1] == p["sv"][1]
+    assert p["solve"][1] == n_it + p["sv"][1]
+    # refine_after = 0: never
+    cs0 = make(lgk, case, refine_after=0, profile=1)
+    p0 = lgk.fetch_profile(lgk.solve_weightings(cs0, W, rho, tol=0.0, max_iter=300))
+    assert p0["sv"][1] == 0 and p0["solve"][1] == 300
