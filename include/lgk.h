@@ -148,15 +148,26 @@ typedef struct {
                                 solves of that case and count.  The configurations sum in
                                 different orders, so plans then differ in rounding from an
                                 untuned solve.  0 (default): the fixed rule.                 */
-    int refine_after;        /* BF16 forms with solve_refine = 0: once a solve has run this many
-                                iterations with columns still active (a stream: once its
-                                oldest running column has), it continues with one refinement
-                                step per iteration (as solve_refine = 1), for every column,
-                                to the end of the solve.  Columns whose residuals level off
-                                above tol (the explicit-inverse solve's accuracy floor, near
-                                5e-5 on the 5000 x 61600 case) then converge.  Needs S's three
-                                BF16 terms (6 m^2 device bytes, kept whenever this is > 0).
-                                0 = never.  Default 4000.                                    */
+    int refine_after;        /* BF16 forms with solve_refine = 0: a column that has run this many
+                                iterations of its weighting (counted from the weighting's own
+                                start, also in a stream) continues with one refinement step of
+                                the solve per iteration (as solve_refine = 1) until it stops.
+                                The other columns feed a zero correction to the refinement
+                                (their arithmetic is bitwise the unrefined one), so a
+                                weighting's plan does not depend on the columns beside it.
+                                Columns whose residuals level off above tol (the explicit-
+                                inverse solve's accuracy floor, near 5e-5 on the 5000 x 61600
+                                case) then converge.  The refined iteration costs two more
+                                solve-sized products for every column once any column needs
+                                it.  Needs S's three BF16 terms (6 m^2 device bytes, kept
+                                whenever this is > 0).  0 = never.  Default 4000.             */
+    int l2_keep_inverse;     /* BF16 forms: 1 keeps S^{-1}'s three BF16 terms (6 m^2 bytes) in L2
+                                across iterations while a solve runs: a persisting L2 carve-out
+                                of up to the device's limit (cudaLimitPersistingL2CacheSize, a
+                                setting of the calling process's context, set back to 0 when
+                                the solve returns) and evict-last loads of the inverse in the
+                                solve.  Changes no result.  Concurrent solves in one process
+                                share the carve-out.  0 (default): default L2 policy.         */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */

@@ -83,6 +83,7 @@ int lgk_default_params(lgk_params* p) {
     p->check_fp64 = 0;
     p->autotune = 0;
     p->refine_after = 4000;
+    p->l2_keep_inverse = 0;
     return LGK_OK;
 }
 
@@ -101,6 +102,8 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     if (prm.check_fp64 != 0 && prm.check_fp64 != 1) return fail(LGK_EINVAL, "check_fp64 must be 0 or 1");
     if (prm.autotune != 0 && prm.autotune != 1) return fail(LGK_EINVAL, "autotune must be 0 or 1");
     if (prm.refine_after < 0) return fail(LGK_EINVAL, "refine_after must be >= 0");
+    if (prm.l2_keep_inverse != 0 && prm.l2_keep_inverse != 1)
+        return fail(LGK_EINVAL, "l2_keep_inverse must be 0 or 1");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

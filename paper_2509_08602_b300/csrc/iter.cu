@@ -213,7 +213,10 @@ __device__ inline void split3_store(const float v[4], __nv_bfloat16* d, size_t p
 // Refinement of the solve (lgk_params.solve_refine): e = rhs - S v, with
 // rhs kept in FP32 by k_reduce_rhs and S v summed from the S . V3 product's
 // stream-K slots; e goes into the solve's input planes (three BF16 terms) for
-// the next product with S^{-1}.  Grid (m_pad / 256, Kp), 64 threads.
+// the next product with S^{-1}.  A column whose refinement is off
+// (refine_on = 0: refine_after, the column is younger than the limit) gets
+// e = 0, so its correction S^{-1} e is exactly zero and its v is bitwise the
+// unrefined solve's.  Grid (m_pad / 256, Kp), 64 threads.
 __global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const float* __restrict__ rhs32,
                                                    __nv_bfloat16* rhs) {
     pdl_trigger();
@@ -223,7 +226,8 @@ __global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const
     const size_t o = (size_t)j * cx.m_pad + i;
     const float4 sv = gemm_out4(src, i, j);
     const float4 b = *reinterpret_cast<const float4*>(rhs32 + o);
-    const float e[4] = {b.x - sv.x, b.y - sv.y, b.z - sv.z, b.w - sv.w};
+    float e[4] = {b.x - sv.x, b.y - sv.y, b.z - sv.z, b.w - sv.w};
+    if (cx.refine_on[j] == 0.f) e[0] = e[1] = e[2] = e[3] = 0.f;
     split3_store(e, rhs + o, (size_t)cx.Kp * cx.m_pad);
 }
 
@@ -531,6 +535,7 @@ static IterCtx make_ctx(ResultData& r) {
     cx.rho = r.colp.as<float>();
     cx.inv_rho = r.colp.as<float>() + r.Kp;
     cx.wbot = r.colp.as<float>() + 2 * r.Kp;
+    cx.refine_on = r.colp.as<float>() + 3 * r.Kp;
     cx.Dr = cs.Dr.as<double>();
     cx.q1 = r.q1.as<float>(); cx.q2 = r.q2.as<float>();
     cx.active = r.active.as<int>(); cx.iters = r.iters.as<int>();
@@ -739,6 +744,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         colp[j] = (float)rh;
         colp[Kp + j] = (float)(1.0 / rh);
         colp[2 * Kp + j] = (float)wB;
+        colp[3 * Kp + j] = cs.prm.solve_refine > 0 ? 1.0f : 0.0f;   // refined from the start, or by age
     };
     for (int j = 0; j < K; ++j) fill_col(j, W + 4 * (size_t)j, rho[j], &cnt[(size_t)j * S]);
     for (int s = 0; s < S; ++s) utab[(size_t)Kp * S + s] = cs.c_of_slot[s];
@@ -756,6 +762,40 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     r.refine_steps = bf16 && cs.S3.p ? cs.prm.solve_refine : 0;
     if (r.refine_steps) {
         if ((rc = r.rhs32.alloc(mq * 4)) || (rc = r.rv.alloc(mq * 4)) || (rc = r.V3.alloc(mq * 6))) return rc;
+    }
+    // S^{-1} kept in L2 across iterations (lgk_params.l2_keep_inverse): a
+    // persisting carve-out of the L2 (a setting of this process's context,
+    // released when the solve ends) and an access-policy window over the
+    // inverse's terms on the solve's launches, which load it evict-last
+    struct L2Release {
+        ResultData& r;
+        ~L2Release() {
+            if (!r.l2_keep) return;
+            cudaCtxResetPersistingL2Cache();
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+            cudaGetLastError();
+            r.l2_keep = false;
+        }
+    } l2_release{r};
+    r.l2_keep = false;
+    if (bf16 && cs.prm.l2_keep_inverse && cs.G3.p) {
+        int max_keep = 0, max_win = 0;
+        if (cudaDeviceGetAttribute(&max_keep, cudaDevAttrMaxPersistingL2CacheSize, cs.device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, cs.device) == cudaSuccess &&
+            max_keep > 0 && max_win > 0) {
+            const size_t win = std::min(cs.G3.bytes, (size_t)max_win);
+            const size_t keep = std::min(win, (size_t)max_keep);
+            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, keep) == cudaSuccess) {
+                r.l2win = cudaAccessPolicyWindow{};
+                r.l2win.base_ptr = cs.G3.p;
+                r.l2win.num_bytes = win;
+                r.l2win.hitRatio = (float)((double)keep / (double)win);
+                r.l2win.hitProp = cudaAccessPropertyPersisting;
+                r.l2win.missProp = cudaAccessPropertyStreaming;
+                r.l2_keep = true;
+            }
+        }
+        cudaGetLastError();
     }
     if (r.refine) {
         if ((rc = r.c1.alloc(mq * 4)) || (rc = r.c2.alloc(nq * 4))) return rc;
@@ -1294,6 +1334,26 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
             if ((rc = tc_prepare(r))) break;
             cx = make_ctx(r);
             if ((rc = capture())) break;
+        }
+        if (r.refine_steps > 0 && cs.prm.solve_refine == 0) {
+            // refine_after applies per column, by the column's own age, so a
+            // weighting's arithmetic does not depend on what else runs beside
+            // it (a stream refills columns; a younger column keeps e = 0)
+            bool flip = false;
+            for (int j = 0; j < Kp; ++j) {
+                const bool holds = stream ? tag_of[j] >= 0 : j < K;
+                const int own = hc->iter - (stream ? start_it[j] : 0);
+                const float on = holds && own >= cs.prm.refine_after ? 1.0f : 0.0f;
+                if (colp[3 * (size_t)Kp + j] != on) {
+                    colp[3 * (size_t)Kp + j] = on;
+                    flip = true;
+                }
+            }
+            if (flip) {
+                LGK_CUDA_TRY(cudaMemcpyAsync(r.colp.as<float>() + 3 * (size_t)Kp, colp.data() + 3 * (size_t)Kp,
+                                             (size_t)Kp * 4, cudaMemcpyHostToDevice, st));
+                LGK_CUDA_TRY(cudaStreamSynchronize(st));
+            }
         }
     }
     cudaFreeHost(hc);

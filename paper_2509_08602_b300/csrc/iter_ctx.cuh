@@ -19,6 +19,7 @@ struct IterCtx {
     const float* rho;       // colp[0]
     const float* inv_rho;   // colp[1]
     const float* wbot;      // colp[2]
+    const float* refine_on; // colp[3]: 1 where the column's solve is refined (solve refinement)
     const double* Dr;
     float* q1;
     float* q2;

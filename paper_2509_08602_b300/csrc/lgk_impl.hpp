@@ -127,6 +127,8 @@ struct ResultData {
     int force_wide = -1;      // autotuner: -1 the default rule, 0 / 1 forced (where allowed)
     DevBuf c1, c2;            // float [Kp][m_pad] lo R1_hi, [Kp][n_pad] lo^T V_hi (last full iteration)
     int refine_steps = 0;     // solve refinement steps per iteration (lgk_params.solve_refine)
+    bool l2_keep = false;     // l2_keep_inverse: the solve's S^{-1} loads persist in an L2 carve-out
+    cudaAccessPolicyWindow l2win{};   // the window over S^{-1}'s terms
     DevBuf rhs32, rv, V3;     // refinement: rhs FP32 [Kp][m_pad], v so far FP32, v as bf16 [3][Kp][m_pad]
     DevBuf mask;              // uint32 [n_pad][mask_words] point selection, when given
     int mask_words = 0;       // 0: every point in every column

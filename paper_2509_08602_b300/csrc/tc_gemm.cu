@@ -70,6 +70,7 @@ struct TcArgs {
     int stage_bytes;
     int out_ld;             // EPI_STORE: rows of the output matrix (m_pad or n_pad)
     int first_only;         // do the work only in the solve's first iteration (else return)
+    int keep_a;             // load A with an evict-last L2 policy (S^{-1} kept in L2 across iterations)
     float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
     void* out;              // EPI_STORE: float [Kp][out_ld];
                             // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
@@ -189,7 +190,7 @@ __device__ inline void epi_resid(float res[kChunk][5], float* red, double* dst, 
 // sub-tiles of 128 rows; an MN-major tile is two 64-row boxes.
 template <int NA, int NT, bool A_MN, int EPI, int MT>
 __device__ inline void load_a_stage(const CUtensorMap* tmA, uint32_t st, uint32_t full, int row0, int kx,
-                                    uint64_t pol_a) {
+                                    uint64_t pol_a, bool keep) {
     if (A_MN) {
 #pragma unroll
         for (int p = 0; p < NA; ++p)
@@ -200,10 +201,15 @@ __device__ inline void load_a_stage(const CUtensorMap* tmA, uint32_t st, uint32_
                 tma_load_3d_hint(dst + kABytes / 2, tmA, row0 + h * 128 + 64, kx, p, full, pol_a);
             }
     } else if (EPI == EPI_PARTIAL && NT == 6) {
-        // the solve: S^{-1} is re-read every iteration, default policy
-        // (an evict-last hint did not keep its 6 m^2 bytes in L2)
+        // the solve: S^{-1} is re-read every iteration: default policy, or
+        // evict-last when a persisting L2 carve-out holds it (keep_a)
+        if (keep) {
 #pragma unroll
-        for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, tmA, kx, row0, p, full);
+            for (int p = 0; p < NA; ++p) tma_load_3d_hint(st + p * kABytes, tmA, kx, row0, p, full, pol_a);
+        } else {
+#pragma unroll
+            for (int p = 0; p < NA; ++p) tma_load_3d(st + p * kABytes, tmA, kx, row0, p, full);
+        }
     } else {
 #pragma unroll
         for (int p = 0; p < NA; ++p)
@@ -261,14 +267,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!a.first_only && warp == 0 && lane == 0) {
         prefetch_tmap(&tmA);
         prefetch_tmap(&tmB);
-        const uint64_t pol_a = policy_evict_first();
+        const uint64_t pol_a = a.keep_a ? policy_evict_last() : policy_evict_first();
         for (int sg = s0; sg < s1 && pre < S; ++sg) {
             const int* g = a.seg + 5 * sg;
             for (int kb = g[2]; kb < g[3] && pre < S; ++kb, ++pre) {
                 const uint32_t full = smem_u32(&bars[pre]);
                 mbar_expect_tx_only(full, a_bytes);
                 load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, smem_u32(smem + (size_t)pre * a.stage_bytes), full,
-                                                    g[0] * 128 * MT, kb * 64, pol_a);
+                                                    g[0] * 128 * MT, kb * 64, pol_a, a.keep_a != 0);
             }
         }
     }
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int it = 0;
         // A streams through once per launch; the B operand, S^{-1} and the
         // epilogue's state should outlive it in L2
-        const uint64_t pol_a = policy_evict_first();
+        const uint64_t pol_a = a.keep_a ? policy_evict_last() : policy_evict_first();
         for (int sg = s0; sg < s1 && ok; ++sg) {
             const int* g = a.seg + 5 * sg;
             const int row0 = g[0] * 128 * MT, col0 = g[1] * a.n_tile;
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
                     if (!ok) break;
                     mbar_expect_tx(full, (uint32_t)a.stage_bytes);
-                    load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, st, full, row0, kx, pol_a);
+                    load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, st, full, row0, kx, pol_a, a.keep_a != 0);
                 }
                 const uint32_t sb = st + a_bytes;
 #pragma unroll
@@ -611,7 +617,7 @@ static int launch_in(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPla
 
 template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
-                  void* out, bool pdl, bool first_only = false) {
+                  void* out, bool pdl, bool first_only = false, bool keep_a = false) {
     if (P.mt != MT) {
         set_error("tensor-core GEMM: plan built for another tile height");
         return LGK_EINVAL;
@@ -641,9 +647,11 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
         set_error("tensor-core GEMM: accumulators exceed tensor memory");
         return LGK_EINVAL;
     }
+    a.keep_a = keep_a && r.l2_keep;
     size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
-    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem,
-                          r.cs->stream, pdl, mA, mB, a, make_ctx_public(r)));
+    LGK_CUDA_TRY(launch_k_win(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem,
+                              r.cs->stream, pdl, a.keep_a ? &r.l2win : nullptr, mA, mB, a,
+                              make_ctx_public(r)));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -738,7 +746,7 @@ int tc_gemm1(ResultData& r, bool pdl) {
 }
 
 int tc_solve(ResultData& r, bool pdl) {
-    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr, pdl);
+    return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.G3, r.maps.rhs, r.plan_s, r, nullptr, pdl, false, true);
 }
 
 // One EPI_PARTIAL product outside a solve's iteration (the plan check): the

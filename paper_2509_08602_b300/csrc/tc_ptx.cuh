@@ -95,6 +95,14 @@ __device__ inline uint64_t policy_evict_first() {
     return p;
 }
 
+// L2 policy for data re-read every iteration that should stay in L2 (S^{-1}
+// in the solve, with a persisting carve-out set on the device).
+__device__ inline uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
