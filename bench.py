@@ -521,6 +521,8 @@ def run_ours(args, rank, world, local):
             "two_pass": bench_two_pass(lgk, case, W, args, local)}
         if not args.no_k441 and args.workload == "cfg1":
             extra["k441"] = bench_k441(lgk, args, local)
+        if not args.no_group and args.workload == "cfg1":
+            extra["group"] = bench_group(lgk, args, local, with_cfg3=args.group_cfg3)
         if not args.no_serve and args.workload == "cfg1":
             sv = serve_run(lgk, args, local, n_cases=24, rate=1.0, workers=2)
             sv["note"] = ("a short stream of the serving workload (bench.py --serve N sweeps the "
@@ -633,6 +635,70 @@ def bench_k441(lgk, args, local, width=128, steps=2, fp32_max_iter=4000):
                                               + case.struct_id.nbytes + W.nbytes),
                     "d2h_bytes_per_step": int(s2["t"].nbytes + s2["tau"].nbytes)},
             "fp32_form": fp32}
+
+
+def bench_group(lgk, args, local, with_cfg3=False):
+    """Co-scheduled cases (lgk_solve_group): the 3750 x 41200 case with its 81
+    weightings and the 500 x 4660 sphere case with its 9 (and, with_cfg3, the
+    9-target 8325 x 122664 case with its 441, all three refining the solve),
+    each as one batch, every tensor-core product of an iteration one launch
+    over all of them; against the same batches solved one after another.
+    Plans are counted by the residual test and the FP64 check as in the main
+    line; the group's plans equal the sequential ones bitwise (checked)."""
+    import torch
+    from synth import cases as SC
+    cfgs = [1, 0] + ([3] if with_cfg3 else [])
+    refine = args.precision == "bf16x3" and not args.exact
+    kn = dict(knobs(args), refine_after=0)
+    if with_cfg3:
+        kn["solve_refine"] = max(1, args.solve_refine)
+    prec = PRECISIONS[args.precision]
+    cases, Ws, rho0 = [], [], []
+    for c in cfgs:
+        case, W = make_inputs(c)
+        cs = lgk.create_case(case.phi, case.kind, case.struct_id, case.n_iso, case.d_presc, case.q_area,
+                             case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
+                             params=lgk.default_params(precision=prec, device=local, lo_refresh=int(refine),
+                                                       check_every=args.check_every, **kn))
+        cases.append(cs)
+        Ws.append(W)
+        rho0.append(RHO0_PER_BETA * cs.beta)
+    kw = dict(w0_bot=SC.W0_BOT, tol=args.tol, max_iter=args.max_iter)
+
+    def counted(res):
+        n = 0
+        for r in res:
+            n += int(passes(lgk.fetch_stats(r), lgk.fetch_check(r), args.tol).sum())
+        return n
+
+    for r in lgk.solve_group(cases, Ws, None, rho0=rho0, **kw):       # untimed: graphs, plans
+        r.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grp = lgk.solve_group(cases, Ws, None, rho0=rho0, **kw)
+    torch.cuda.synchronize()
+    t_group = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq = [lgk.solve_weightings(c, W, None, rho0=r0, **kw) for c, W, r0 in zip(cases, Ws, rho0)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    same = all(np.array_equal(lgk.fetch_stats(a)["obj"], lgk.fetch_stats(b)["obj"]) for a, b in zip(grp, seq))
+    n_g, n_s = counted(grp), counted(seq)
+    members = []
+    for c, cs, W, r in zip(cfgs, cases, Ws, grp):
+        st = lgk.fetch_stats(r)
+        members.append({"case": f"{SC.WORKLOADS[c]['name']} (A {cs.m}x{cs.n})", "K": int(W.shape[0]),
+                        "max_iters": int(st["iters"].max()), "mean_iters": float(st["iters"].mean())})
+    for r in grp + seq:
+        r.close()
+    for cs in cases:
+        cs.close()
+    plans = sum(int(W.shape[0]) for W in Ws)
+    return {"value": n_g / t_group, "unit": "plans/s", "plans": plans, "converged": n_g,
+            "seconds": t_group, "sequential": {"value": n_s / t_seq, "seconds": t_seq, "converged": n_s},
+            "speedup": t_seq / t_group, "bitwise_equal_to_sequential": bool(same), "members": members,
+            "solve_refine": kn["solve_refine"],
+            "note": "one batch per case; the group ends when its slowest member's slowest column stops"}
 
 
 def check_summary(checks):
@@ -933,6 +999,10 @@ def main():
                     help="count plans by the residual test alone (no FP64 check in the timed region)")
     ap.add_argument("--l2-keep-inverse", action="store_true",
                     help="keep S^-1 in a persisting L2 carve-out during solves (lgk_params.l2_keep_inverse)")
+    ap.add_argument("--no-group", action="store_true",
+                    help="skip the co-scheduled group measurement (lgk_solve_group) of the cfg1 line")
+    ap.add_argument("--group-cfg3", action="store_true",
+                    help="add the 9-target 8325 x 122664 case (441 weightings) to the group measurement")
     ap.add_argument("--no-k441", action="store_true",
                     help="skip the 441-weighting (5000 x 61600) measurement of the cfg1 line")
     ap.add_argument("--serve", type=int, default=0,

@@ -224,6 +224,33 @@ int lgk_solve_weightings(lgk_case* cs, int K, const double* W, const double* rho
                          lgk_result** out);
 
 /*
+ * lgk_solve_group -- G (1..4) cases of different sizes solved together, each
+ * with its own weighting set, every tensor-core product of an iteration one
+ * persistent launch over all of them (the co-scheduled batched form: a small
+ * case's products ride in the launches of a large one instead of paying
+ * their own ramp and tail), captured in CUDA graphs.  Each case runs the
+ * iteration of lgk_solve_weightings (Sec. 2.B, Eq. admm) on its own K columns
+ * with its own control block and stop test; every case's products are cut
+ * into the same stream-K runs and summed in the same order as in a solve of
+ * that case alone, so each result is bitwise that of lgk_solve_weightings
+ * with the same arguments (except that the long-solve switches
+ * lo_refresh_iters and refine_after do not apply, and autotune is ignored).
+ *   cases: G distinct cases on one device; all BF16 forms with the same
+ *          lo_refresh, solve_refine and check_every (else LGK_EINVAL).
+ *   K, W, rho: per case, as in lgk_solve_weightings (rho may be NULL, or
+ *          rho[g] NULL, for Eq. rho_rule with w0_bot and rho0[g]).
+ *   tol, max_iter: shared by the group.
+ *   out: G result handles (host array), each freed with lgk_free_result.
+ * The group runs on the first case's stream.  256-row tiles are used only
+ * when every case can take them.  On error no result is returned.
+ * Errors: LGK_EINVAL, LGK_ENOMEM, LGK_ECUDA, LGK_ETIMEOUT (the first case's
+ * timeout_ms bounds the whole group).
+ */
+int lgk_solve_group(int G, lgk_case* const* cases, const int* K, const double* const* W,
+                    const double* const* rho, double w0_bot, const double* rho0, double tol,
+                    int max_iter, lgk_result** out);
+
+/*
  * lgk_solve_weightings_async -- lgk_solve_weightings without blocking.
  *
  * Same arguments, checks and iteration (Sec. 2.B) as lgk_solve_weightings;

@@ -249,6 +249,62 @@ int lgk_solve_weightings_masked(lgk_case* c, int K, const double* W, const doubl
     return LGK_OK;
 }
 
+int lgk_solve_group(int G, lgk_case* const* cases, const int* K, const double* const* W,
+                    const double* const* rho, double w0_bot, const double* rho0, double tol, int max_iter,
+                    lgk_result** out) {
+    if (!out) return fail(LGK_EINVAL, "out is NULL");
+    if (G < 1 || G > 4) return fail(LGK_EINVAL, "need 1 <= G <= 4");
+    for (int g = 0; g < G; ++g) out[g] = nullptr;
+    if (!cases || !K || !W) return fail(LGK_EINVAL, "cases, K or W is NULL");
+    if (!(tol >= 0.0) || !isfinite(tol) || max_iter < 1) return fail(LGK_EINVAL, "need tol >= 0, max_iter >= 1");
+    std::vector<std::vector<double>> rr(G);
+    for (int g = 0; g < G; ++g) {
+        if (!cases[g] || !W[g]) return fail(LGK_EINVAL, "a case or its W is NULL");
+        for (int h = 0; h < g; ++h)
+            if (cases[h] == cases[g]) return fail(LGK_EINVAL, "a case appears twice in the group");
+        if (int rb = case_free(cases[g])) return rb;
+        if (K[g] < 1 || K[g] > 4096) return fail(LGK_EINVAL, "need 1 <= K <= 4096 per case");
+        if (!finite_nonneg(W[g], (size_t)K[g] * 4)) return fail(LGK_EINVAL, "weights must be finite and >= 0");
+        int rrc = column_rho(K[g], W[g], rho ? rho[g] : nullptr, w0_bot, rho0 ? rho0[g] : 0.0, rr[g]);
+        if (rrc) return rrc;
+    }
+    LGK_CUDA_TRY(cudaSetDevice(cases[0]->d->device));
+    std::vector<std::unique_ptr<ResultData>> res(G);
+    std::vector<ResultData*> raw(G);
+    int rc = LGK_OK;
+    try {
+        for (int g = 0; g < G && !rc; ++g) {
+            res[g].reset(new ResultData);
+            res[g]->cs = cases[g]->d;
+            res[g]->K = K[g];
+            res[g]->tol = tol;
+            res[g]->max_iter = max_iter;
+            raw[g] = res[g].get();
+            if (cases[g]->d->device != cases[0]->d->device)
+                rc = fail(LGK_EINVAL, "a group's cases must share one device");
+            else
+                rc = run_solve(*res[g], W[g], rr[g].data(), nullptr, nullptr, nullptr, nullptr, true);
+        }
+        if (!rc) rc = run_group(G, raw.data());
+    } catch (const std::bad_alloc&) {
+        rc = fail(LGK_ENOMEM, "host allocation failed");
+    }
+    if (rc) return rc;
+    std::vector<lgk_result*> hs(G, nullptr);
+    for (int g = 0; g < G; ++g) {
+        hs[g] = new (std::nothrow) lgk_result;
+        if (!hs[g]) {
+            for (int h = 0; h < g; ++h) delete hs[h];
+            return fail(LGK_ENOMEM, "host allocation failed");
+        }
+    }
+    for (int g = 0; g < G; ++g) {
+        hs[g]->d = std::move(res[g]);
+        out[g] = hs[g];
+    }
+    return LGK_OK;
+}
+
 int lgk_solve_weightings_warm(lgk_case* c, int K, const double* W, const double* rho, double w0_bot,
                               double rho0, double tol, int max_iter, const double* q1_init,
                               const double* q2_init, lgk_result** out) {

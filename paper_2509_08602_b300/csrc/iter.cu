@@ -328,59 +328,19 @@ __global__ void __launch_bounds__(128) k_q1_update(IterCtx cx, SumSrc src, void*
     }
 }
 
-// Per-column stop test and bookkeeping; the last kernel of every iteration.
-// One block per column sums that column's residual partials (fixed order,
-// deterministic); the last block to finish (ticket) updates the control
-// block.
+// Per-column stop test and bookkeeping; the last kernel of an iteration whose
+// GEMM2 does not do it itself (residual-test iterations, the FP32 form,
+// groups).  One block per column sums that column's residual partials (fixed
+// order, deterministic); the last block to finish (ticket) updates the
+// control block.
 __global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
     pdl_trigger();
     pdl_wait();
     Control* c = cx.ctrl;
     if (c->n_active == 0) return;
-    const int j = blockIdx.x, it = c->iter + 1;
-    const bool err = c->err != 0;
-    const bool check = (cx.tol > 0.f && it % cx.check_every == 0) || it >= c->max_iter;
-    const bool test = cx.tol > 0.f && it % cx.check_every == 0;
-    __shared__ double red[5][4];
-    if (err) {
-        if (threadIdx.x == 0) cx.active[j] = 0;
-    } else if (cx.active[j]) {
-        bool stop = it >= c->max_iter;
-        if (check) {
-            const int nb = cx.n_resid_n + cx.n_resid_m;
-            double s5[5] = {0, 0, 0, 0, 0};
-            for (int b = threadIdx.x; b < nb; b += blockDim.x)
-#pragma unroll
-                for (int k = 0; k < 5; ++k) s5[k] += cx.resid[((size_t)b * cx.Kp + j) * 5 + k];
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                double v = s5[k];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) red[k][w] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t5[5];
-                for (int k = 0; k < 5; ++k) t5[k] = red[k][0] + red[k][1] + red[k][2] + red[k][3];
-                const double sq = sqrt((double)(cx.n + cx.m_rows));
-                const double rho = cx.rho[j];
-                const double rn = sqrt(t5[0]), xn = sqrt(t5[1]), zn = sqrt(t5[2]);
-                const double sn = rho * sqrt(t5[3]), yn = rho * sqrt(t5[4]);
-                const double xz = fmax(xn, zn);
-                cx.stats[j] = rn / fmax(xz, 1e-300);
-                cx.stats[cx.Kp + j] = sn / fmax(yn, 1e-300);
-                if (test && rn <= cx.eps_abs * sq + cx.tol * xz && sn <= cx.eps_abs * sq + cx.tol * yn) {
-                    stop = true;
-                    cx.active[cx.Kp + j] = 1;   // converged
-                }
-            }
-        }
-        if (threadIdx.x == 0) {
-            cx.iters[j] = it;
-            if (stop) cx.active[j] = 0;
-        }
-    }
+    const int it = c->iter + 1;
+    __shared__ double red[5 * 4];
+    finalize_column(cx, blockIdx.x, it, c->err != 0, red);
     // last block: count the active columns, advance the iteration counter
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -391,18 +351,7 @@ __global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
     if (!last) return;
     __threadfence();
     __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    int mine = 0;
-    for (int k = threadIdx.x; k < cx.Kp; k += blockDim.x) mine += ((volatile int*)cx.active)[k] != 0;
-    atomicAdd(&cnt, mine);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        c->n_active = cnt;
-        c->iter = it;
-        c->ticket = 0;
-        __threadfence();
-    }
+    finalize_count(cx, it, &cnt);
 }
 
 // c^T z1 in FP64 per column (deterministic block reduction).
@@ -675,16 +624,22 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     if (full && (rc = tc_gemm2_lo(r, pdl, first_only))) return rc;
     ran(full);
     next();
-    if ((rc = tc_gemm2(r, pdl))) return rc;
+    // between residual tests the finalize step (iteration counters, the
+    // iteration cap) runs in GEMM2's last CTA instead of its own kernel
+    const bool fold = !test_slot;
+    if ((rc = tc_gemm2(r, pdl, fold))) return rc;
     next();
-    LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
-    LGK_LAUNCH_CHECK();
+    if (!fold) {
+        LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
+        LGK_LAUNCH_CHECK();
+    }
+    ran(!fold);
     next();
     return LGK_OK;
 }
 
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init, const uint32_t* mask, const StreamSpec* stream) {
+              const double* q2_init, const uint32_t* mask, const StreamSpec* stream, bool prepare_only) {
     CaseData& cs = *r.cs;
     cudaStream_t st = cs.stream;
     const bool bf16 = cs.prm.precision != LGK_PREC_FP32;
@@ -778,7 +733,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         }
     } l2_release{r};
     r.l2_keep = false;
-    if (bf16 && cs.prm.l2_keep_inverse && cs.G3.p) {
+    if (bf16 && cs.prm.l2_keep_inverse && cs.G3.p && !prepare_only) {
         int max_keep = 0, max_win = 0;
         if (cudaDeviceGetAttribute(&max_keep, cudaDevAttrMaxPersistingL2CacheSize, cs.device) == cudaSuccess &&
             cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, cs.device) == cudaSuccess &&
@@ -872,7 +827,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     std::vector<std::pair<int, int>> cands;
     size_t tune_next = 0;
     std::vector<float> tune_ms;
-    if (bf16 && cs.prm.autotune) {
+    if (bf16 && cs.prm.autotune && !prepare_only) {
         std::lock_guard<std::mutex> lk(cs.tune_mu);
         auto it = cs.tuned.find(Kp);
         if (it != cs.tuned.end()) {
@@ -893,6 +848,12 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         if ((rc = tc_prepare(r))) return rc;
     } else {
         cublasSetStream(cs.cublas, st);
+    }
+    // a group solve (run_group) takes over from here with its own graph
+    if (prepare_only) {
+        r.colp_h = colp;
+        LGK_CUDA_TRY(cudaStreamSynchronize(st));
+        return LGK_OK;
     }
 
     // capture a CUDA graph of `per_graph` iterations, replay until done
@@ -1364,6 +1325,177 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     if (stream && (rc = flush_checks())) return rc;
     k_objective<<<Kp, 256, 0, st>>>(cx, r.stats.as<double>() + 2 * Kp);
     LGK_LAUNCH_CHECK();
+    LGK_CUDA_TRY(cudaStreamSynchronize(st));
+    return LGK_OK;
+}
+
+// ------------------------------------------------------------ group solve
+
+static int fail_status(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+// One iteration of a group (the sequence of iteration_bf16): every tensor-core
+// product is one launch over all G solves; the element-wise kernels run per
+// solve, back to back on the group's stream.
+static int iteration_group(int G, ResultData* const* R, const IterCtx* cx, cudaStream_t st, int itx) {
+    const ResultData& r0 = *R[0];
+    const int check_every = r0.cs->prm.check_every;
+    const bool test_slot = (itx + 1) % check_every == 0;
+    const bool full = r0.refine && (itx == 0 || test_slot);
+    const bool first_only = itx == 0 && !test_slot;
+    const bool pdl = true;
+    int rc;
+    if (full && (rc = tc_group_gemm1_lo(G, R, st, pdl && itx > 0, first_only))) return rc;
+    if ((rc = tc_group_gemm1(G, R, st, pdl && (itx > 0 || full)))) return rc;
+    for (int g = 0; g < G; ++g) {
+        ResultData& r = *R[g];
+        const dim3 gm(r.cs->m_pad / 256, r.Kp);
+        float* rhs32 = r.refine_steps ? r.rhs32.as<float>() : nullptr;
+        LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(64), 0, st, pdl, cx[g], plan_src(r, r.plan1), r.rhs.p,
+                              rhs32));
+        LGK_LAUNCH_CHECK();
+    }
+    if ((rc = tc_group_solve(G, R, st, pdl))) return rc;
+    const int steps = r0.refine_steps;
+    for (int g = 0; g < G; ++g) {
+        ResultData& r = *R[g];
+        const dim3 gm(r.cs->m_pad / 256, r.Kp);
+        __nv_bfloat16* V3 = steps ? r.V3.as<__nv_bfloat16>() : nullptr;
+        float* rv = steps ? r.rv.as<float>() : nullptr;
+        if (steps == 0)
+            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_PLAIN>, gm, dim3(64), 0, st, pdl, cx[g],
+                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
+        else
+            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FIRST>, gm, dim3(64), 0, st, pdl, cx[g],
+                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
+        LGK_LAUNCH_CHECK();
+    }
+    for (int step = 1; step <= steps; ++step) {
+        if ((rc = tc_group_sv(G, R, st, pdl))) return rc;
+        for (int g = 0; g < G; ++g) {
+            ResultData& r = *R[g];
+            const dim3 gm(r.cs->m_pad / 256, r.Kp);
+            LGK_CUDA_TRY(launch_k(k_reduce_err, gm, dim3(64), 0, st, pdl, cx[g], plan_src(r, r.plan_s),
+                                  r.rhs32.as<float>(), r.rhs.as<__nv_bfloat16>()));
+            LGK_LAUNCH_CHECK();
+        }
+        if ((rc = tc_group_solve(G, R, st, pdl))) return rc;
+        for (int g = 0; g < G; ++g) {
+            ResultData& r = *R[g];
+            const dim3 gm(r.cs->m_pad / 256, r.Kp);
+            if (step < steps)
+                LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_ACCUM>, gm, dim3(64), 0, st, pdl, cx[g],
+                                      plan_src(r, r.plan_s), r.V.p, r.rv.as<float>(), r.V3.as<__nv_bfloat16>()));
+            else
+                LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FINAL>, gm, dim3(64), 0, st, pdl, cx[g],
+                                      plan_src(r, r.plan_s), r.V.p, r.rv.as<float>(), r.V3.as<__nv_bfloat16>()));
+            LGK_LAUNCH_CHECK();
+        }
+    }
+    if (full && (rc = tc_group_gemm2_lo(G, R, st, pdl, first_only))) return rc;
+    if ((rc = tc_group_gemm2(G, R, st, pdl))) return rc;
+    for (int g = 0; g < G; ++g) {
+        LGK_CUDA_TRY(launch_k(k_finalize, dim3(R[g]->Kp), dim3(128), 0, st, pdl, cx[g]));
+        LGK_LAUNCH_CHECK();
+    }
+    return LGK_OK;
+}
+
+int run_group(int G, ResultData* const* R) {
+    if (G < 1 || G > 4) return fail_status(LGK_EINVAL, "a group holds 1 to 4 solves");
+    const ResultData& r0 = *R[0];
+    const CaseData& c0 = *r0.cs;
+    for (int g = 0; g < G; ++g) {
+        const ResultData& r = *R[g];
+        const CaseData& cs = *r.cs;
+        if (cs.prm.precision == LGK_PREC_FP32)
+            return fail_status(LGK_EINVAL, "group solves run the BF16 forms only");
+        if (cs.device != c0.device) return fail_status(LGK_EINVAL, "a group's cases must share one device");
+        if (cs.na != c0.na || r.refine != r0.refine || r.refine_steps != r0.refine_steps ||
+            cs.prm.check_every != c0.prm.check_every || r.mask_words)
+            return fail_status(LGK_EINVAL, "a group's solves must share the iteration form (BF16 terms, lagged "
+                                           "low term, solve refinement, residual-test spacing)");
+    }
+    int rc;
+    // one tile height for all: 256-row tiles only if every solve can take them
+    bool all_wide = true;
+    for (int g = 0; g < G; ++g) all_wide = all_wide && R[g]->wide;
+    for (int g = 0; g < G; ++g)
+        if (R[g]->wide != all_wide) {
+            R[g]->force_wide = 0;
+            if ((rc = tc_prepare(*R[g]))) return rc;
+        }
+    cudaStream_t st = c0.stream;
+    const int per_graph = std::max(1, std::min(r0.max_iter, 5 * c0.prm.check_every));
+    std::vector<IterCtx> cx(G);
+    for (int g = 0; g < G; ++g) cx[g] = make_ctx(*R[g]);
+    // the group's graph of per_graph iterations
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < per_graph; ++it) {
+        if ((rc = iteration_group(G, R, cx.data(), st, it))) {
+            cudaStreamEndCapture(st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+    }
+    LGK_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+    size_t n_all = 0, n_nodes = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n_all) == cudaSuccess && n_all) {
+        std::vector<cudaGraphNode_t> nodes(n_all);
+        if (cudaGraphGetNodes(graph, nodes.data(), &n_all) == cudaSuccess)
+            for (auto nd : nodes) {
+                cudaGraphNodeType ty;
+                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
+            }
+    }
+    count_launch(-(long long)n_nodes);
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail_status(LGK_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+    } guard{exec};
+    Control* hc = nullptr;
+    LGK_CUDA_TRY(cudaMallocHost(&hc, sizeof(Control) * G));
+    struct HostGuard {
+        Control* p;
+        ~HostGuard() { if (p) cudaFreeHost(p); }
+    } hguard{hc};
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t le = cudaGraphLaunch(exec, st);
+        if (le != cudaSuccess) return fail_status(LGK_ECUDA, cudaGetErrorString(le));
+        count_launch((long long)n_nodes);
+        for (int g = 0; g < G; ++g)
+            LGK_CUDA_TRY(cudaMemcpyAsync(hc + g, R[g]->ctrl.p, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        for (;;) {
+            cudaError_t q = cudaStreamQuery(st);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return fail_status(LGK_ECUDA, cudaGetErrorString(q));
+            auto el = std::chrono::steady_clock::now() - t0;
+            if (std::chrono::duration_cast<std::chrono::milliseconds>(el).count() > c0.prm.timeout_ms)
+                return fail_status(LGK_ETIMEOUT, "group solve exceeded timeout_ms");
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        bool any = false;
+        for (int g = 0; g < G; ++g) {
+            if (hc[g].err)
+                return fail_status(LGK_ECUDA, "device error flag " + std::to_string(hc[g].err) +
+                                                  " raised during the group solve (case " + std::to_string(g) + ")");
+            any = any || hc[g].n_active != 0;
+        }
+        if (!any) break;
+    }
+    for (int g = 0; g < G; ++g) {
+        ResultData& r = *R[g];
+        k_objective<<<r.Kp, 256, 0, st>>>(cx[g], r.stats.as<double>() + 2 * r.Kp);
+        LGK_LAUNCH_CHECK();
+    }
     LGK_CUDA_TRY(cudaStreamSynchronize(st));
     return LGK_OK;
 }

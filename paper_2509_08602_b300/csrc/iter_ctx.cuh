@@ -46,6 +46,77 @@ __device__ inline bool is_check_iter(const Control* c, int check_every, float to
     return (tol > 0.f && it % check_every == 0) || it >= c->max_iter;
 }
 
+// Stop test of column j after iteration `it` (Boyd et al. Sec. 3.3 on the
+// residual partials of the n- and m-blocks, summed in a fixed order), run by
+// all threads of the calling block (blockDim.x a multiple of 32, at most 32
+// warps); red: 5 x (blockDim.x / 32) doubles of shared memory.  Records the
+// column's iteration count and clears its active flag when it stops.
+__device__ inline void finalize_column(const IterCtx& cx, int j, int it, bool err, double* red) {
+    const bool check = (cx.tol > 0.f && it % cx.check_every == 0) || it >= cx.ctrl->max_iter;
+    const bool test = cx.tol > 0.f && it % cx.check_every == 0;
+    const int nw = blockDim.x >> 5;
+    if (err) {
+        if (threadIdx.x == 0) cx.active[j] = 0;
+    } else if (cx.active[j]) {
+        bool stop = it >= cx.ctrl->max_iter;
+        if (check) {
+            const int nb = cx.n_resid_n + cx.n_resid_m;
+            double s5[5] = {0, 0, 0, 0, 0};
+            for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) s5[k] += cx.resid[((size_t)b * cx.Kp + j) * 5 + k];
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                double v = s5[k];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[k * nw + w] = v;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t5[5];
+                for (int k = 0; k < 5; ++k) {
+                    t5[k] = 0.0;
+                    for (int q = 0; q < nw; ++q) t5[k] += red[k * nw + q];
+                }
+                const double sq = sqrt((double)(cx.n + cx.m_rows));
+                const double rho = cx.rho[j];
+                const double rn = sqrt(t5[0]), xn = sqrt(t5[1]), zn = sqrt(t5[2]);
+                const double sn = rho * sqrt(t5[3]), yn = rho * sqrt(t5[4]);
+                const double xz = fmax(xn, zn);
+                cx.stats[j] = rn / fmax(xz, 1e-300);
+                cx.stats[cx.Kp + j] = sn / fmax(yn, 1e-300);
+                if (test && rn <= cx.eps_abs * sq + cx.tol * xz && sn <= cx.eps_abs * sq + cx.tol * yn) {
+                    stop = true;
+                    cx.active[cx.Kp + j] = 1;   // converged
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            cx.iters[j] = it;
+            if (stop) cx.active[j] = 0;
+        }
+    }
+}
+
+// After every column's finalize_column (and a fence): count the active
+// columns and advance the iteration counter (one block; cnt: a shared int).
+__device__ inline void finalize_count(const IterCtx& cx, int it, int* cnt) {
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int k = threadIdx.x; k < cx.Kp; k += blockDim.x) mine += ((volatile int*)cx.active)[k] != 0;
+    atomicAdd(cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Control* c = cx.ctrl;
+        c->n_active = *cnt;
+        c->iter = it;
+        c->ticket = 0;
+        __threadfence();
+    }
+}
+
 __device__ inline float b_of(int i, int j, int n_beams, int m, const double* Dr, const float* wbot) {
     return (i >= n_beams && i < m) ? (float)(wbot[j] * Dr[i]) : 0.0f;
 }

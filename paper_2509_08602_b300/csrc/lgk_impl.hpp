@@ -200,8 +200,16 @@ struct StreamSpec {
 };
 
 // one solve (iter.cu); with `stream`, W and rho hold its first r.K weightings
+// prepare_only: set up the solve's tables, state, plans and maps and return
+// before capturing its graph (a group solve, run_group, runs the iterations)
 int run_solve(ResultData& r, const double* W, const double* rho, const double* q1_init,
-              const double* q2_init, const uint32_t* mask, const StreamSpec* stream = nullptr);
+              const double* q2_init, const uint32_t* mask, const StreamSpec* stream = nullptr,
+              bool prepare_only = false);
+// Group solve: G (<= 4) prepared batch solves of different cases on one
+// device, every tensor-core GEMM of an iteration one launch over all of them
+// (iter.cu).  Same iteration form, tolerance, iteration cap and residual-test
+// spacing for all; each keeps its own control block and stops on its own.
+int run_group(int G, ResultData* const* R);
 int fetch_times(const ResultData& r, double* t, double* tau);
 int fetch_doses(const ResultData& r, const double* phi_eval, int n_eval, double* dose);
 int fetch_stats(const ResultData& r, int* iters, double* obj, double* rel_pri,
@@ -247,6 +255,15 @@ int tc_gemm1_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_gemm2_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_solve(ResultData& r, bool pdl = false);     // part[s] = G3 . rhs^T  (6 products)
 int tc_sv(ResultData& r, bool pdl = false);        // part[s] = S3 . V3^T   (6 products, refinement)
-int tc_gemm2(ResultData& r, bool pdl = false);     // fused: q1, R1 update from Ahat^T . V
+// fused: q1, R1 update from Ahat^T . V; fold: the kernel also runs the
+// iteration's finalize step (stop tests, counters) in its last CTA
+int tc_gemm2(ResultData& r, bool pdl = false, bool fold = false);
+// the same products over a group of solves, one launch each, on stream st
+int tc_group_gemm1(int G, ResultData* const* R, cudaStream_t st, bool pdl);
+int tc_group_gemm1_lo(int G, ResultData* const* R, cudaStream_t st, bool pdl, bool first_only);
+int tc_group_solve(int G, ResultData* const* R, cudaStream_t st, bool pdl);
+int tc_group_sv(int G, ResultData* const* R, cudaStream_t st, bool pdl);
+int tc_group_gemm2_lo(int G, ResultData* const* R, cudaStream_t st, bool pdl, bool first_only);
+int tc_group_gemm2(int G, ResultData* const* R, cudaStream_t st, bool pdl);
 
 }  // namespace lgk

@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <string>
 
 #include "iter_ctx.cuh"
@@ -71,6 +72,9 @@ struct TcArgs {
     int out_ld;             // EPI_STORE: rows of the output matrix (m_pad or n_pad)
     int first_only;         // do the work only in the solve's first iteration (else return)
     int keep_a;             // load A with an evict-last L2 policy (S^{-1} kept in L2 across iterations)
+    int ncta;               // CTAs with a run in this case's plan (the rest skip the case)
+    int fold_finalize;      // EPI_Q1, one case: the last CTA to finish runs the iteration's
+                            // finalize step (stop tests, counters) instead of a separate kernel
     float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
     void* out;              // EPI_STORE: float [Kp][out_ld];
                             // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
@@ -219,38 +223,52 @@ __device__ inline void load_a_stage(const CUtensorMap* tmA, uint32_t st, uint32_
     }
 }
 
+// Up to kMaxGroup cases in one launch (a co-scheduled group solve, Sec. 2.B's
+// K columns generalised to several matrices): every CTA runs its stream-K run
+// of case 0's units, then its run of case 1's, and so on, through one
+// continuous TMA / MMA / epilogue pipeline (no drain between cases).  Each
+// case's plan is cut into its own equal runs, so the group stays balanced and
+// every case's tiles are summed exactly as in a launch of that case alone.
+constexpr int kMaxGroup = 4;
+struct TcGroup {
+    CUtensorMap tmA[kMaxGroup];
+    CUtensorMap tmB[kMaxGroup];
+    TcArgs a[kMaxGroup];      // stages, stage_bytes, tmem_cols, nbuf, first_only, keep_a: launch-wide (a[0])
+    IterCtx cx[kMaxGroup];
+    int G;
+};
+static_assert(sizeof(TcGroup) <= 4096, "kernel parameters of a group launch exceed 4 KB");
+
 // MT: 128-row sub-tiles per output tile.  MT = 2 puts two accumulators side by
 // side (256 rows) on one B tile: half the B traffic per A byte, and twice the
 // A bytes per pipeline stage, so more of A is in flight per SM (the one-term-A
 // GEMMs are otherwise limited by how much of A the stage ring holds).
 template <int NA, int NB, int NT, bool A_MN, int EPI, int MT>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcArgs a, IterCtx cx) {
+__global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__ TcGroup P) {
     pdl_trigger();
-    Control* ctrl = cx.ctrl;
+    const TcArgs& a0 = P.a[0];
+    const int G = P.G;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int S = a.stages;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * a.stage_bytes);
+    const int S = a0.stages;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * a0.stage_bytes);
     // bars: [0, S) stage full, [S, 2S) stage empty, 2S + b accumulator b full,
     // 2S + 4 + b accumulator b drained (b < nbuf <= 4)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 8);
     int* sh_last = reinterpret_cast<int*>(bars + 2 * S + 8) + 1;
-    float* red = reinterpret_cast<float*>(bars + 2 * S + 9);        // [8 warps][kChunk][5]
-    const int NBUF = a.nbuf;
+    int* sh_run = reinterpret_cast<int*>(bars + 2 * S + 9);         // bit g: case g has work
+    float* red = reinterpret_cast<float*>(bars + 2 * S + 10);       // [8 warps][kChunk][5]
+    const int NBUF = a0.nbuf;
+    const int TC = a0.tmem_cols;                                    // columns of one accumulator
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
-    int* err = &ctrl->err;
-    const int b_bytes = a.n_tile * 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2 * S + 4; ++s) mbar_init(smem_u32(&bars[s]), 1);
         for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[2 * S + 4 + b]), 8);   // one per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * MT * a.tmem_cols);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NBUF * MT * TC);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -261,63 +279,86 @@ __global__ void __launch_bounds__(kThreads, 1)
     // tail.  Their bytes are added to the stage's full barrier as a pending
     // transaction without an arrival: the stage cannot complete before the
     // arrival that comes with its B tile, after the wait.  (Not for launches
-    // that work only in the solve's first iteration: they mostly do nothing.)
+    // that work only in the solve's first iteration: they mostly do nothing;
+    // not for groups.)
     const uint32_t a_bytes = (uint32_t)(NA * MT * kABytes);
     int pre = 0;
-    if (!a.first_only && warp == 0 && lane == 0) {
-        prefetch_tmap(&tmA);
-        prefetch_tmap(&tmB);
-        const uint64_t pol_a = a.keep_a ? policy_evict_last() : policy_evict_first();
+    if (G == 1 && !a0.first_only && warp == 0 && lane == 0 && (int)blockIdx.x < a0.ncta) {
+        const int s0 = a0.cta_seg[blockIdx.x], s1 = a0.cta_seg[blockIdx.x + 1];
+        prefetch_tmap(&P.tmA[0]);
+        prefetch_tmap(&P.tmB[0]);
+        const uint64_t pol_a = a0.keep_a ? policy_evict_last() : policy_evict_first();
         for (int sg = s0; sg < s1 && pre < S; ++sg) {
-            const int* g = a.seg + 5 * sg;
+            const int* g = a0.seg + 5 * sg;
             for (int kb = g[2]; kb < g[3] && pre < S; ++kb, ++pre) {
                 const uint32_t full = smem_u32(&bars[pre]);
                 mbar_expect_tx_only(full, a_bytes);
-                load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, smem_u32(smem + (size_t)pre * a.stage_bytes), full,
-                                                    g[0] * 128 * MT, kb * 64, pol_a, a.keep_a != 0);
+                load_a_stage<NA, NT, A_MN, EPI, MT>(&P.tmA[0], smem_u32(smem + (size_t)pre * a0.stage_bytes), full,
+                                                    g[0] * 128 * MT, kb * 64, pol_a, a0.keep_a != 0);
             }
         }
     }
     // set-up done; from here on the previous kernel's output is read
     pdl_wait();
-    const bool run = ctrl->n_active != 0 && ctrl->err == 0 && (!a.first_only || ctrl->iter == 0);
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int g = 0; g < G; ++g) {
+            const Control* c = P.cx[g].ctrl;
+            if ((int)blockIdx.x < P.a[g].ncta && c->n_active != 0 && c->err == 0 &&
+                (!a0.first_only || c->iter == 0))
+                m |= 1 << g;
+        }
+        *sh_run = m;
+    }
+    __syncthreads();
+    const int runmask = *sh_run;
 
-    if (!run) {
-        // every column has stopped (or an error is pending): nothing to do
-        // but let the prefetched A tiles land (bounded) before the CTA exits
-        if (warp == 0 && lane == 0)
+    if (warp == 0 && lane == 0) {
+        int* err = &P.cx[0].ctrl->err;
+        if (pre > 0 && !(runmask & 1)) {
+            // the one case has stopped (or an error is pending): nothing to do
+            // but let the prefetched A tiles land (bounded) before the CTA exits
             for (int s = 0; s < pre; ++s) {
                 mbar_arrive(smem_u32(&bars[s]));
                 mbar_wait(smem_u32(&bars[s]), 0u, err);
             }
-    } else if (warp == 0 && lane == 0) {
+        }
         // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
         int it = 0;
         // A streams through once per launch; the B operand, S^{-1} and the
         // epilogue's state should outlive it in L2
-        const uint64_t pol_a = a.keep_a ? policy_evict_last() : policy_evict_first();
-        for (int sg = s0; sg < s1 && ok; ++sg) {
-            const int* g = a.seg + 5 * sg;
-            const int row0 = g[0] * 128 * MT, col0 = g[1] * a.n_tile;
-            for (int kb = g[2]; kb < g[3] && ok; ++kb, ++it) {
-                const int s = it % S;
-                const uint32_t ph = (uint32_t)(it / S) & 1u;
-                const uint32_t full = smem_u32(&bars[s]);
-                const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-                const int kx = kb * 64;
-                if (it < pre) {
-                    // A already in flight (prefetched): the arrival and the B bytes
-                    mbar_expect_tx(full, (uint32_t)a.stage_bytes - a_bytes);
-                } else {
-                    ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
-                    if (!ok) break;
-                    mbar_expect_tx(full, (uint32_t)a.stage_bytes);
-                    load_a_stage<NA, NT, A_MN, EPI, MT>(&tmA, st, full, row0, kx, pol_a, a.keep_a != 0);
-                }
-                const uint32_t sb = st + a_bytes;
+        const uint64_t pol_a = a0.keep_a ? policy_evict_last() : policy_evict_first();
 #pragma unroll
-                for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &tmB, kx, col0, p, full);
+        for (int gi = 0; gi < kMaxGroup; ++gi) {
+            if (gi >= G || !ok) break;
+            if (!((runmask >> gi) & 1)) continue;
+            const TcArgs& a = P.a[gi];
+            err = &P.cx[gi].ctrl->err;
+            const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
+            const int b_bytes = a.n_tile * 128;
+            for (int sg = s0; sg < s1 && ok; ++sg) {
+                const int* g = a.seg + 5 * sg;
+                const int row0 = g[0] * 128 * MT, col0 = g[1] * a.n_tile;
+                for (int kb = g[2]; kb < g[3] && ok; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    const uint32_t full = smem_u32(&bars[s]);
+                    const uint32_t st = smem_u32(smem + (size_t)s * a0.stage_bytes);
+                    const int kx = kb * 64;
+                    if (it < pre) {
+                        // A already in flight (prefetched): the arrival and the B bytes
+                        mbar_expect_tx(full, a_bytes + (uint32_t)(NB * b_bytes) - a_bytes);
+                    } else {
+                        ok = mbar_wait(smem_u32(&bars[S + s]), ph ^ 1u, err);
+                        if (!ok) break;
+                        mbar_expect_tx(full, a_bytes + (uint32_t)(NB * b_bytes));
+                        load_a_stage<NA, NT, A_MN, EPI, MT>(&P.tmA[gi], st, full, row0, kx, pol_a, a0.keep_a != 0);
+                    }
+                    const uint32_t sb = st + a_bytes;
+#pragma unroll
+                    for (int p = 0; p < NB; ++p) tma_load_3d(sb + p * b_bytes, &P.tmB[gi], kx, col0, p, full);
+                }
             }
         }
         // drain: wait (bounded) for the copies of the last issued stages
@@ -325,43 +366,52 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = mbar_wait(smem_u32(&bars[j % S]), (uint32_t)(j / S) & 1u, err);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
-        const uint32_t idesc = instr_desc(a.n_tile, A_MN);
         bool ok = true;
-        int it = 0;
-        for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
-            const int* g = a.seg + 5 * sg;
-            const int b = u % NBUF;
-            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 4 + b]), (uint32_t)((u / NBUF) & 1) ^ 1u, err);
-            tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(b * MT * a.tmem_cols);
-            for (int kb = g[2]; kb < g[3]; ++kb, ++it) {
-                const int s = it % S;
-                const uint32_t ph = (uint32_t)(it / S) & 1u;
-                if (ok) ok = mbar_wait(smem_u32(&bars[s]), ph, err);
+        int it = 0, u = 0;
+#pragma unroll
+        for (int gi = 0; gi < kMaxGroup; ++gi) {
+            if (gi >= G) break;
+            if (!((runmask >> gi) & 1)) continue;
+            const TcArgs& a = P.a[gi];
+            int* err = &P.cx[gi].ctrl->err;
+            const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
+            const int b_bytes = a.n_tile * 128;
+            const uint32_t idesc = instr_desc(a.n_tile, A_MN);
+            for (int sg = s0; sg < s1; ++sg, ++u) {
+                const int* g = a.seg + 5 * sg;
+                const int b = u % NBUF;
+                if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + 4 + b]), (uint32_t)((u / NBUF) & 1) ^ 1u, err);
                 tc_fence_after();
-                const uint32_t st = smem_u32(smem + (size_t)s * a.stage_bytes);
-                const uint32_t sb = st + NA * MT * kABytes;
-                if (ok) {
+                const uint32_t d = tmem + (uint32_t)(b * MT * TC);
+                for (int kb = g[2]; kb < g[3]; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (uint32_t)(it / S) & 1u;
+                    if (ok) ok = mbar_wait(smem_u32(&bars[s]), ph, err);
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + (size_t)s * a0.stage_bytes);
+                    const uint32_t sb = st + NA * MT * kABytes;
+                    if (ok) {
 #pragma unroll
-                    for (int t = 0; t < NT; ++t) {
-                        const uint32_t sbt = sb + term_b(NT, t) * b_bytes;
+                        for (int t = 0; t < NT; ++t) {
+                            const uint32_t sbt = sb + term_b(NT, t) * b_bytes;
 #pragma unroll
-                        for (int h = 0; h < MT; ++h) {
-                            const uint32_t sa = st + (term_a(NT, t) * MT + h) * kABytes;
+                            for (int h = 0; h < MT; ++h) {
+                                const uint32_t sa = st + (term_a(NT, t) * MT + h) * kABytes;
 #pragma unroll
-                            for (int ks = 0; ks < 4; ++ks) {
-                                uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
-                                                   : smem_desc(sa + ks * 32, 16, 1024);
-                                uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
-                                tc_mma(d + (uint32_t)(h * a.tmem_cols), ad, bd, idesc,
-                                       (kb > g[2] || t > 0 || ks > 0) ? 1u : 0u);
+                                for (int ks = 0; ks < 4; ++ks) {
+                                    uint64_t ad = A_MN ? smem_desc(sa + ks * 2048, kABytes / 2, 1024)
+                                                       : smem_desc(sa + ks * 32, 16, 1024);
+                                    uint64_t bd = smem_desc(sbt + ks * 32, 16, 1024);
+                                    tc_mma(d + (uint32_t)(h * TC), ad, bd, idesc,
+                                           (kb > g[2] || t > 0 || ks > 0) ? 1u : 0u);
+                                }
                             }
                         }
                     }
+                    tc_commit(smem_u32(&bars[S + s]));      // frees the stage when its MMAs finish
                 }
-                tc_commit(smem_u32(&bars[S + s]));      // frees the stage when its MMAs finish
+                tc_commit(smem_u32(&bars[2 * S + b]));      // accumulator b complete
             }
-            tc_commit(smem_u32(&bars[2 * S + b]));      // accumulator b complete
         }
     } else if (warp >= 2) {
         // ---------------- epilogue (8 warps)
@@ -370,100 +420,111 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int et = threadIdx.x - 64;                // 0..255
         const int r = ew * 32 + lane;                   // row within the 128-row sub-tile
         const int hrow = MT == 2 ? hf : 0;              // this warp's 128-row sub-tile
-        const int half = a.n_tile / 2;                  // multiple of kChunk
-        const int cbeg = MT == 2 ? 0 : hf * half, cend = MT == 2 ? a.n_tile : cbeg + half;
-        const bool check = EPI == EPI_Q1 && is_check_iter(ctrl, cx.check_every, cx.tol);
         bool ok = true;
-        for (int sg = s0, u = 0; sg < s1; ++sg, ++u) {
-            const int b = u % NBUF;
-            const int* g = a.seg + 5 * sg;
-            const int rt = g[0], ct = g[1], slot = g[4];
-            const int tile = ct * a.row_tiles + rt;
-            const int sb = a.tile_begin[tile], se = a.tile_begin[tile + 1];
-            const int row = (rt * MT + hrow) * 128 + r, col0 = ct * a.n_tile;
-            double* rdst = cx.resid +
-                           ((size_t)(rt * MT + hrow) * cx.Kp + col0) * 5;
-            if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
-            tc_fence_after();
-            const uint32_t base =
-                tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((b * MT + hrow) * a.tmem_cols);
-            if (EPI == EPI_PARTIAL || se - sb > 1) {
-                // store this segment's partial sum in its slot ([slot][MT][n_tile][128])
-                float* own = a.part + ((size_t)slot * MT + hrow) * a.n_tile * 128 + r;
-                for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
-                    float v[kChunk];
-                    tmem_ld8(base + (uint32_t)c0, v);
+        int u = 0;
 #pragma unroll
-                    for (int c = 0; c < kChunk; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
-                if (EPI != EPI_PARTIAL) {
-                    // the CTA completing the tile sums its slots in k order
-                    __threadfence();
-                    epi_bar();
-                    if (et == 0) *sh_last = atomicAdd(&a.tile_count[tile], 1) == se - sb - 1;
-                    epi_bar();
-                    if (*sh_last) {
-                        __threadfence();
-                        for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
-                            float v[kChunk], res[kChunk][5];
+        for (int gi = 0; gi < kMaxGroup; ++gi) {
+            if (gi >= G) break;
+            if (!((runmask >> gi) & 1)) continue;
+            const TcArgs& a = P.a[gi];
+            const IterCtx& cx = P.cx[gi];
+            int* err = &cx.ctrl->err;
+            const int s0 = a.cta_seg[blockIdx.x], s1 = a.cta_seg[blockIdx.x + 1];
+            const int half = a.n_tile / 2;              // multiple of kChunk
+            const int cbeg = MT == 2 ? 0 : hf * half, cend = MT == 2 ? a.n_tile : cbeg + half;
+            const bool check = EPI == EPI_Q1 && is_check_iter(cx.ctrl, cx.check_every, cx.tol);
+            for (int sg = s0; sg < s1; ++sg, ++u) {
+                const int b = u % NBUF;
+                const int* g = a.seg + 5 * sg;
+                const int rt = g[0], ct = g[1], slot = g[4];
+                const int tile = ct * a.row_tiles + rt;
+                const int sb = a.tile_begin[tile], se = a.tile_begin[tile + 1];
+                const int row = (rt * MT + hrow) * 128 + r, col0 = ct * a.n_tile;
+                double* rdst = cx.resid +
+                               ((size_t)(rt * MT + hrow) * cx.Kp + col0) * 5;
+                if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
+                tc_fence_after();
+                const uint32_t base =
+                    tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)((b * MT + hrow) * TC);
+                if (EPI == EPI_PARTIAL || se - sb > 1) {
+                    // store this segment's partial sum in its slot ([slot][MT][n_tile][128])
+                    float* own = a.part + ((size_t)slot * MT + hrow) * a.n_tile * 128 + r;
+                    for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                        float v[kChunk];
+                        tmem_ld8(base + (uint32_t)c0, v);
 #pragma unroll
-                            for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
-                            for (int k = sb; k < se; ++k) {
-                                const float* ps = a.part + ((size_t)a.tile_slots[k] * MT + hrow) * a.n_tile * 128 + r;
-#pragma unroll
-                                for (int c = 0; c < kChunk; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
-                            }
-                            epi_op<EPI>(cx, a, row, col0 + c0, v, res);
-                            if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
-                        }
-                        if (et == 0) a.tile_count[tile] = 0;
+                        for (int c = 0; c < kChunk; ++c) own[(size_t)(c0 + c) * 128] = ok ? v[c] : 0.f;
                     }
-                    epi_bar();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
+                    if (EPI != EPI_PARTIAL) {
+                        // the CTA completing the tile sums its slots in k order
+                        __threadfence();
+                        epi_bar();
+                        if (et == 0) *sh_last = atomicAdd(&a.tile_count[tile], 1) == se - sb - 1;
+                        epi_bar();
+                        if (*sh_last) {
+                            __threadfence();
+                            for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                                float v[kChunk], res[kChunk][5];
+#pragma unroll
+                                for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
+                                for (int k = sb; k < se; ++k) {
+                                    const float* ps =
+                                        a.part + ((size_t)a.tile_slots[k] * MT + hrow) * a.n_tile * 128 + r;
+#pragma unroll
+                                    for (int c = 0; c < kChunk; ++c) v[c] += __ldcg(ps + (size_t)(c0 + c) * 128);
+                                }
+                                epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                                if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
+                            }
+                            if (et == 0) a.tile_count[tile] = 0;
+                        }
+                        epi_bar();
+                    }
+                } else if (EPI == EPI_Q1) {
+                    // the whole k range of the tile is in this accumulator; the
+                    // next chunk's inputs load while this one is finished
+                    // (two named buffers, unrolled by two, so both stay in registers)
+                    Q1In inA, inB;
+                    float vA[kChunk], vB[kChunk], res[kChunk][5];
+                    q1_load(cx, row, col0 + cbeg, inA);
+                    tmem_ld8(base + (uint32_t)cbeg, vA);
+                    for (int c0 = cbeg; c0 < cend; c0 += 2 * kChunk) {
+                        const bool moreB = c0 + kChunk < cend;
+                        if (moreB) q1_load(cx, row, col0 + c0 + kChunk, inB);
+                        if (!ok)
+                            for (int c = 0; c < kChunk; ++c) vA[c] = 0.f;
+                        q1_finish(cx, a, row, col0 + c0, vA, inA, res);
+                        if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
+                        if (!moreB) break;
+                        tmem_ld8(base + (uint32_t)(c0 + kChunk), vB);
+                        const bool moreA = c0 + 2 * kChunk < cend;
+                        if (moreA) q1_load(cx, row, col0 + c0 + 2 * kChunk, inA);
+                        if (!ok)
+                            for (int c = 0; c < kChunk; ++c) vB[c] = 0.f;
+                        q1_finish(cx, a, row, col0 + c0 + kChunk, vB, inB, res);
+                        if (check) epi_resid(res, red, rdst + (c0 + kChunk) * 5, lane, ew, hf, et);
+                        if (moreA) tmem_ld8(base + (uint32_t)(c0 + 2 * kChunk), vA);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
+                } else {
+                    // the whole k range of the tile is in this accumulator
+                    for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
+                        float v[kChunk], res[kChunk][5];
+                        tmem_ld8(base + (uint32_t)c0, v);
+                        if (!ok)
+                            for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
+                        epi_op<EPI>(cx, a, row, col0 + c0, v, res);
+                        if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
                 }
-            } else if (EPI == EPI_Q1) {
-                // the whole k range of the tile is in this accumulator; the
-                // next chunk's inputs load while this one is finished
-                // (two named buffers, unrolled by two, so both stay in registers)
-                Q1In inA, inB;
-                float vA[kChunk], vB[kChunk], res[kChunk][5];
-                q1_load(cx, row, col0 + cbeg, inA);
-                tmem_ld8(base + (uint32_t)cbeg, vA);
-                for (int c0 = cbeg; c0 < cend; c0 += 2 * kChunk) {
-                    const bool moreB = c0 + kChunk < cend;
-                    if (moreB) q1_load(cx, row, col0 + c0 + kChunk, inB);
-                    if (!ok)
-                        for (int c = 0; c < kChunk; ++c) vA[c] = 0.f;
-                    q1_finish(cx, a, row, col0 + c0, vA, inA, res);
-                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
-                    if (!moreB) break;
-                    tmem_ld8(base + (uint32_t)(c0 + kChunk), vB);
-                    const bool moreA = c0 + 2 * kChunk < cend;
-                    if (moreA) q1_load(cx, row, col0 + c0 + 2 * kChunk, inA);
-                    if (!ok)
-                        for (int c = 0; c < kChunk; ++c) vB[c] = 0.f;
-                    q1_finish(cx, a, row, col0 + c0 + kChunk, vB, inB, res);
-                    if (check) epi_resid(res, red, rdst + (c0 + kChunk) * 5, lane, ew, hf, et);
-                    if (moreA) tmem_ld8(base + (uint32_t)(c0 + 2 * kChunk), vA);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
-            } else {
-                // the whole k range of the tile is in this accumulator
-                for (int c0 = cbeg; c0 < cend; c0 += kChunk) {
-                    float v[kChunk], res[kChunk][5];
-                    tmem_ld8(base + (uint32_t)c0, v);
-                    if (!ok)
-                        for (int c = 0; c < kChunk; ++c) v[c] = 0.f;
-                    epi_op<EPI>(cx, a, row, col0 + c0, v, res);
-                    if (check) epi_resid(res, red, rdst + c0 * 5, lane, ew, hf, et);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&bars[2 * S + 4 + b]));
             }
         }
     }
@@ -471,7 +532,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, NBUF * MT * a.tmem_cols);
+        tmem_dealloc(tmem, NBUF * MT * TC);
+    }
+    if (EPI == EPI_Q1 && a0.fold_finalize) {
+        // the iteration's finalize step in the last CTA to finish (every
+        // CTA's epilogue stores are fenced before its ticket)
+        const IterCtx& cx = P.cx[0];
+        Control* c = cx.ctrl;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            *sh_last = atomicAdd(&c->ticket, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (*sh_last) {
+            __threadfence();
+            if (c->n_active != 0) {
+                const int it = c->iter + 1;
+                const bool er = c->err != 0;
+                double* redd = reinterpret_cast<double*>(red);      // 5 x 10 doubles
+                for (int j = 0; j < cx.Kp; ++j) {
+                    finalize_column(cx, j, it, er, redd);
+                    __syncthreads();
+                }
+                __threadfence();
+                finalize_count(cx, it, sh_run);
+            } else if (threadIdx.x == 0) {
+                c->ticket = 0;
+            }
+        }
     }
 }
 
@@ -524,7 +612,7 @@ int make_tma_map(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows,
 
 static constexpr int kSmemLimit = 232448;    // 227 KB opt-in per block
 
-static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 16 + 8 * kChunk * 5 * 4; }
+static int smem_extra() { return 1024 + 8 * (2 * 8 + 8) + 32 + 8 * kChunk * 5 * 4; }
 
 int sm_count() {
     static const int n = [] {
@@ -615,15 +703,9 @@ template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int launch_in(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, CaseData& cs,
                      const IterCtx& cx, float* part, cudaStream_t st);
 
-template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
-static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
-                  void* out, bool pdl, bool first_only = false, bool keep_a = false) {
-    if (P.mt != MT) {
-        set_error("tensor-core GEMM: plan built for another tile height");
-        return LGK_EINVAL;
-    }
+// Per-case arguments of one launch from a plan.
+static TcArgs plan_args(const GemmPlan& P, float* part, void* out, int out_ld) {
     TcArgs a{};
-    a.first_only = first_only;
     a.cta_seg = P.cta_seg;
     a.seg = P.seg;
     a.tile_begin = P.tile_begin;
@@ -631,27 +713,96 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     a.tile_count = P.tile_count;
     a.row_tiles = P.rows;
     a.n_tile = P.n_tile;
-    a.part = r.part.as<float>();
+    a.ncta = P.grid;
+    a.part = part;
     a.out = out;
-    a.out_ld = A_MN ? r.cs->n_pad : r.cs->m_pad;
-    a.stage_bytes = NA * MT * kABytes + NB * a.n_tile * 128;
-    a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
-    if (a.stages < 2) {
+    a.out_ld = out_ld;
+    return a;
+}
+
+// Launch-wide fields (ring stages, accumulators) for the widest case of a
+// group, copied into every case's arguments; returns the dynamic shared
+// memory size, or 0 with the error set.
+template <int NA, int NB, int MT>
+static size_t group_layout(TcGroup& g, bool first_only, bool keep_a) {
+    int nt = 16;
+    for (int i = 0; i < g.G; ++i) nt = std::max(nt, g.a[i].n_tile);
+    const int stage_bytes = NA * MT * kABytes + NB * nt * 128;
+    const int stages = std::min(8, (kSmemLimit - smem_extra()) / stage_bytes);
+    if (stages < 2) {
         set_error("tensor-core GEMM: stage does not fit in shared memory");
-        return LGK_EINVAL;
+        return 0;
     }
-    a.tmem_cols = 32;
-    while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
-    a.nbuf = 4 * MT * a.tmem_cols <= 512 ? 4 : 2;
-    if (a.nbuf * MT * a.tmem_cols > 512) {
+    int tc = 32;
+    while (tc < nt) tc <<= 1;
+    const int nbuf = 4 * MT * tc <= 512 ? 4 : 2;
+    if (nbuf * MT * tc > 512) {
         set_error("tensor-core GEMM: accumulators exceed tensor memory");
+        return 0;
+    }
+    for (int i = 0; i < g.G; ++i) {
+        g.a[i].stage_bytes = stage_bytes;
+        g.a[i].stages = stages;
+        g.a[i].tmem_cols = tc;
+        g.a[i].nbuf = nbuf;
+        g.a[i].first_only = first_only;
+        g.a[i].keep_a = keep_a;
+    }
+    return (size_t)stages * stage_bytes + smem_extra();
+}
+
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
+static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
+                  void* out, bool pdl, bool first_only = false, bool keep_a = false, bool fold = false) {
+    if (P.mt != MT) {
+        set_error("tensor-core GEMM: plan built for another tile height");
         return LGK_EINVAL;
     }
-    a.keep_a = keep_a && r.l2_keep;
-    size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
+    TcGroup g;
+    memset(&g, 0, sizeof(g));
+    g.G = 1;
+    g.tmA[0] = mA;
+    g.tmB[0] = mB;
+    g.a[0] = plan_args(P, r.part.as<float>(), out, A_MN ? r.cs->n_pad : r.cs->m_pad);
+    g.cx[0] = make_ctx_public(r);
+    const bool keep = keep_a && r.l2_keep;
+    const size_t smem = group_layout<NA, NB, MT>(g, first_only, keep);
+    if (!smem) return LGK_EINVAL;
+    g.a[0].fold_finalize = EPI == EPI_Q1 && fold;
     LGK_CUDA_TRY(launch_k_win(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem,
-                              r.cs->stream, pdl, a.keep_a ? &r.l2win : nullptr, mA, mB, a,
-                              make_ctx_public(r)));
+                              r.cs->stream, pdl, keep ? &r.l2win : nullptr, g));
+    LGK_LAUNCH_CHECK();
+    return LGK_OK;
+}
+
+// One launch over the G solves of a group (run_group): each solve's own maps,
+// plan, partial-sum buffer, output and context, on stream st.
+template <int NA, int NB, int NT, bool A_MN, int EPI, int MT>
+static int launch_group(int G, ResultData* const* R, const CUtensorMap* const* mA, const CUtensorMap* const* mB,
+                        const GemmPlan* const* P, void* const* out, cudaStream_t st, bool pdl, bool first_only) {
+    if (G < 1 || G > kMaxGroup) {
+        set_error("tensor-core GEMM: group size out of range");
+        return LGK_EINVAL;
+    }
+    TcGroup g;
+    memset(&g, 0, sizeof(g));
+    g.G = G;
+    int grid = 1;
+    for (int i = 0; i < G; ++i) {
+        if (P[i]->mt != MT) {
+            set_error("tensor-core GEMM: plan built for another tile height");
+            return LGK_EINVAL;
+        }
+        g.tmA[i] = *mA[i];
+        g.tmB[i] = *mB[i];
+        g.a[i] = plan_args(*P[i], R[i]->part.as<float>(), out ? out[i] : nullptr,
+                           A_MN ? R[i]->cs->n_pad : R[i]->cs->m_pad);
+        g.cx[i] = make_ctx_public(*R[i]);
+        grid = std::max(grid, P[i]->grid);
+    }
+    const size_t smem = group_layout<NA, NB, MT>(g, first_only, false);
+    if (!smem) return LGK_EINVAL;
+    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(grid), dim3(kThreads), smem, st, pdl, g));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -755,27 +906,18 @@ int tc_solve(ResultData& r, bool pdl) {
 template <int NA, int NB, int NT, bool A_MN, int EPI, int MT>
 static int launch_in(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, CaseData& cs,
                      const IterCtx& cx, float* part, cudaStream_t st) {
-    TcArgs a{};
-    a.cta_seg = P.cta_seg;
-    a.seg = P.seg;
-    a.tile_begin = P.tile_begin;
-    a.tile_slots = P.tile_slots;
-    a.tile_count = P.tile_count;
-    a.row_tiles = P.rows;
-    a.n_tile = P.n_tile;
-    a.part = part;
-    a.out = nullptr;
-    a.out_ld = A_MN ? cs.n_pad : cs.m_pad;
-    a.stage_bytes = NA * MT * kABytes + NB * a.n_tile * 128;
-    a.stages = std::min(8, (kSmemLimit - smem_extra()) / a.stage_bytes);
-    a.tmem_cols = 32;
-    while (a.tmem_cols < a.n_tile) a.tmem_cols <<= 1;
-    a.nbuf = 4 * MT * a.tmem_cols <= 512 ? 4 : 2;
-    const size_t smem = (size_t)a.stages * a.stage_bytes + smem_extra();
+    TcGroup g;
+    memset(&g, 0, sizeof(g));
+    g.G = 1;
+    g.tmA[0] = mA;
+    g.tmB[0] = mB;
+    g.a[0] = plan_args(P, part, nullptr, A_MN ? cs.n_pad : cs.m_pad);
+    g.cx[0] = cx;
+    const size_t smem = group_layout<NA, NB, MT>(g, false, false);
+    if (!smem) return LGK_EINVAL;
     LGK_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
-    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem, st, false, mA,
-                          mB, a, cx));
+    LGK_CUDA_TRY(launch_k(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem, st, false, g));
     LGK_LAUNCH_CHECK();
     return LGK_OK;
 }
@@ -794,10 +936,88 @@ int tc_sv(ResultData& r, bool pdl) {
     return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.S3, r.maps.V3, r.plan_s, r, nullptr, pdl);
 }
 
-int tc_gemm2(ResultData& r, bool pdl) {
-    if (r.cs->na == 2 && !r.refine) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
-    if (r.plan2.mt == 2) return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
-    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+int tc_gemm2(ResultData& r, bool pdl, bool fold) {
+    if (r.cs->na == 2 && !r.refine)
+        return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
+    if (r.plan2.mt == 2)
+        return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
+    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
 }
+
+}  // namespace lgk
+
+// ------------------------------------------------------------ group launches
+// One launch per product over the G solves of a group (run_group checks that
+// they share the form: BF16 terms of A, lagged low term, tile height).
+
+namespace lgk {
+
+namespace {
+struct GroupOps {
+    ResultData* const* R;
+    int G;
+    const CUtensorMap* a[kMaxGroup];
+    const CUtensorMap* b[kMaxGroup];
+    const GemmPlan* p[kMaxGroup];
+    void* out[kMaxGroup];
+};
+}  // namespace
+
+#define LGK_GROUP_OPS(EXPR_A, EXPR_B, EXPR_P, EXPR_OUT)      \
+    GroupOps o;                                              \
+    o.R = R;                                                 \
+    o.G = G;                                                 \
+    for (int i = 0; i < G && i < kMaxGroup; ++i) {           \
+        ResultData& r = *R[i];                               \
+        (void)r;                                             \
+        o.a[i] = &(EXPR_A);                                  \
+        o.b[i] = &(EXPR_B);                                  \
+        o.p[i] = &(EXPR_P);                                  \
+        o.out[i] = (EXPR_OUT);                               \
+    }
+
+int tc_group_gemm1(int G, ResultData* const* R, cudaStream_t st, bool pdl) {
+    LGK_GROUP_OPS(r.maps.A_k, r.maps.R1, r.plan1, nullptr);
+    const ResultData& r0 = *R[0];
+    if (r0.cs->na == 2 && !r0.refine)
+        return launch_group<2, 2, 3, false, EPI_PARTIAL, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+    if (r0.wide) return launch_group<1, 2, 2, false, EPI_PARTIAL, 2>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+    return launch_group<1, 2, 2, false, EPI_PARTIAL, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+}
+
+int tc_group_gemm1_lo(int G, ResultData* const* R, cudaStream_t st, bool pdl, bool first_only) {
+    LGK_GROUP_OPS(r.maps.Alo_k, r.maps.R1, r.plan1, r.c1.p);
+    if (R[0]->wide)
+        return launch_group<1, 1, 1, false, EPI_STORE, 2>(G, R, o.a, o.b, o.p, o.out, st, pdl, first_only);
+    return launch_group<1, 1, 1, false, EPI_STORE, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, first_only);
+}
+
+int tc_group_solve(int G, ResultData* const* R, cudaStream_t st, bool pdl) {
+    LGK_GROUP_OPS(r.maps.G3, r.maps.rhs, r.plan_s, nullptr);
+    return launch_group<3, 3, 6, false, EPI_PARTIAL, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+}
+
+int tc_group_sv(int G, ResultData* const* R, cudaStream_t st, bool pdl) {
+    LGK_GROUP_OPS(r.maps.S3, r.maps.V3, r.plan_s, nullptr);
+    return launch_group<3, 3, 6, false, EPI_PARTIAL, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+}
+
+int tc_group_gemm2_lo(int G, ResultData* const* R, cudaStream_t st, bool pdl, bool first_only) {
+    LGK_GROUP_OPS(r.maps.Alo_mn, r.maps.V, r.plan2, r.c2.p);
+    if (R[0]->plan2.mt == 2)
+        return launch_group<1, 1, 1, true, EPI_STORE, 2>(G, R, o.a, o.b, o.p, o.out, st, pdl, first_only);
+    return launch_group<1, 1, 1, true, EPI_STORE, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, first_only);
+}
+
+int tc_group_gemm2(int G, ResultData* const* R, cudaStream_t st, bool pdl) {
+    LGK_GROUP_OPS(r.maps.A_mn, r.maps.V, r.plan2, r.R1.p);
+    const ResultData& r0 = *R[0];
+    if (r0.cs->na == 2 && !r0.refine)
+        return launch_group<2, 2, 3, true, EPI_Q1, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+    if (r0.plan2.mt == 2) return launch_group<1, 2, 2, true, EPI_Q1, 2>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+    return launch_group<1, 2, 2, true, EPI_Q1, 1>(G, R, o.a, o.b, o.p, o.out, st, pdl, false);
+}
+
+#undef LGK_GROUP_OPS
 
 }  // namespace lgk

@@ -101,6 +101,9 @@ def _load():
                                                C.c_double, C.c_double, C.c_double, C.c_int,
                                                P(C.c_void_p)]
     lib.lgk_solve_weightings_async.restype = C.c_int
+    lib.lgk_solve_group.argtypes = [C.c_int, P(C.c_void_p), P(C.c_int), P(P(C.c_double)), P(P(C.c_double)),
+                                    C.c_double, P(C.c_double), C.c_double, C.c_int, P(C.c_void_p)]
+    lib.lgk_solve_group.restype = C.c_int
     lib.lgk_wait.argtypes = [C.c_void_p, C.c_int]
     lib.lgk_wait.restype = C.c_int
     lib.lgk_low_dose_volumes.argtypes = [C.c_void_p, P(C.c_double), C.c_int, C.c_int, P(C.c_double),
@@ -246,6 +249,30 @@ def solve_weightings(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: floa
                                      float(w0_bot), float(rho0), float(tol), int(max_iter),
                                      C.byref(h)))
     return Result(h, K, case)
+
+
+def solve_group(cases, Ws, rhos=None, *, w0_bot: float = 0.0, rho0=None, tol: float = 1e-4,
+                max_iter: int = 10000) -> list:
+    """lgk_solve_group: up to 4 cases, each with its own weightings (Ws[g],
+    K_g x 4), solved together (one launch per product over all of them).
+    rhos: None or per case None / K_g penalties; rho0: per case (Eq. rho_rule).
+    Returns one Result per case."""
+    G = len(cases)
+    Ws = [np.ascontiguousarray(np.atleast_2d(W), dtype=np.float64) for W in Ws]
+    if len(Ws) != G or any(W.shape[1] != 4 for W in Ws):
+        raise LgkError(1, "one K x 4 weight matrix per case")
+    Ks = (C.c_int * G)(*[W.shape[0] for W in Ws])
+    rr = [None] * G if rhos is None else [
+        None if r is None else np.ascontiguousarray(np.broadcast_to(r, (W.shape[0],)), dtype=np.float64)
+        for r, W in zip(rhos, Ws)]
+    hs = (C.c_void_p * G)(*[c._h for c in cases])
+    wp = (C.POINTER(C.c_double) * G)(*[_ptr(W, C.c_double) for W in Ws])
+    rp = (C.POINTER(C.c_double) * G)(*[_ptr(r, C.c_double) for r in rr])
+    r0 = None if rho0 is None else np.ascontiguousarray(np.broadcast_to(rho0, (G,)), dtype=np.float64)
+    out = (C.c_void_p * G)()
+    _check(_lib.lgk_solve_group(G, hs, Ks, wp, rp, float(w0_bot), _ptr(r0, C.c_double), float(tol),
+                                int(max_iter), out))
+    return [Result(C.c_void_p(out[g]), Ws[g].shape[0], cases[g]) for g in range(G)]
 
 
 def solve_weightings_async(case: Case, W, rho=None, *, w0_bot: float = 0.0, rho0: float = 0.0,
