@@ -116,6 +116,11 @@ def test_null_arguments_are_errors_not_crashes(lgk):
     assert lib.lgk_fetch_check(None, None) == 1
     assert lib.lgk_solve_weightings_async(None, 1, None, None, 0.0, 0.0, 0.0, 1, ctypes.byref(h)) == 1
     assert lib.lgk_wait(None, 0) == 1
+    outs = (ctypes.c_void_p * 4)()
+    assert lib.lgk_solve_group(2, None, None, None, None, 0.0, None, 1e-4, 10, outs) == 1
+    assert lib.lgk_solve_group(0, None, None, None, None, 0.0, None, 1e-4, 10, outs) == 1
+    assert lib.lgk_solve_group(5, None, None, None, None, 0.0, None, 1e-4, 10, outs) == 1
+    assert lib.lgk_solve_group(1, None, None, None, None, 0.0, None, 1e-4, 10, None) == 1
     cid = ctypes.c_longlong()
     assert lib.lgk_server_open(None, None, ctypes.byref(cid)) == 1
     assert lib.lgk_server_submit_to(None, 0, 1, None, ctypes.byref(cid)) == 1
