@@ -177,7 +177,7 @@ def allreduce_sum(x, world):
 def knobs(args):
     """lgk_params fields the command line sets for every BF16 case."""
     return dict(solve_refine=args.solve_refine, setup_fp64=int(args.setup_fp64), rho_adapt=int(args.rho_adapt),
-                l2_keep_inverse=int(args.l2_keep_inverse))
+                l2_keep_inverse=int(args.l2_keep_inverse), gemm2_tile_rows=args.gemm2_rows)
 
 
 def passes(st, ck, tol):
@@ -306,7 +306,7 @@ def workload_config(case, W, args):
                 "and add the low term's products from the last test iteration (lo_refresh)"
                 if args.precision == "bf16x3" and not args.exact else ""),
             "solve_refine": args.solve_refine, "rho_adapt": bool(args.rho_adapt),
-            "l2_keep_inverse": bool(args.l2_keep_inverse),
+            "l2_keep_inverse": bool(args.l2_keep_inverse), "gemm2_tile_rows": args.gemm2_rows,
             "schur": "S = I + A A^T on " + ("FP64 CUDA cores" if args.setup_fp64 else "tensor cores (BF16 "
                                              "products, FP32 chunk sums, FP64 across chunks)"),
             "rho": "Eq. rho_rule, rho0 = 1100 beta", "l2": "inputs larger than L2 (A resident, "
@@ -999,6 +999,8 @@ def main():
                     help="count plans by the residual test alone (no FP64 check in the timed region)")
     ap.add_argument("--l2-keep-inverse", action="store_true",
                     help="keep S^-1 in a persisting L2 carve-out during solves (lgk_params.l2_keep_inverse)")
+    ap.add_argument("--gemm2-rows", type=int, default=0, choices=[0, 128, 256],
+                    help="GEMM2 tile height (lgk_params.gemm2_tile_rows; 0: as GEMM1)")
     ap.add_argument("--no-group", action="store_true",
                     help="skip the co-scheduled group measurement (lgk_solve_group) of the cfg1 line")
     ap.add_argument("--group-cfg3", action="store_true",

@@ -168,6 +168,11 @@ typedef struct {
                                 the solve returns) and evict-last loads of the inverse in the
                                 solve.  Changes no result.  Concurrent solves in one process
                                 share the carve-out.  0 (default): default L2 policy.         */
+    int gemm2_tile_rows;     /* BF16 forms: rows of A^T per output tile of GEMM2 (the q1 step's
+                                product), 128 or 256 (256 where the operand and the column
+                                count allow it), or 0 (default) for GEMM1's height.  Changes the
+                                summation order (results differ in rounding).  The autotuner
+                                chooses it on its own.                                        */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */

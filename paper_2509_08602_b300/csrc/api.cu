@@ -84,6 +84,7 @@ int lgk_default_params(lgk_params* p) {
     p->autotune = 0;
     p->refine_after = 4000;
     p->l2_keep_inverse = 0;
+    p->gemm2_tile_rows = 0;
     return LGK_OK;
 }
 
@@ -104,6 +105,8 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
     if (prm.refine_after < 0) return fail(LGK_EINVAL, "refine_after must be >= 0");
     if (prm.l2_keep_inverse != 0 && prm.l2_keep_inverse != 1)
         return fail(LGK_EINVAL, "l2_keep_inverse must be 0 or 1");
+    if (prm.gemm2_tile_rows != 0 && prm.gemm2_tile_rows != 128 && prm.gemm2_tile_rows != 256)
+        return fail(LGK_EINVAL, "gemm2_tile_rows must be 0, 128 or 256");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

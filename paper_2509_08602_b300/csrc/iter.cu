@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <chrono>
 #include <thread>
 #include <vector>
@@ -161,11 +162,10 @@ __global__ void k_init_r1(IterCtx cx, void* R1) {
 // parts (the solve amplifies input rounding).  Four rows per thread; grid
 // (m_pad / 256, Kp), 64 threads.
 template <bool BF16>
-__global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs, float* rhs32) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void reduce_rhs_body(const IterCtx& cx, const SumSrc& src, void* rhs, float* rhs32,
+                                                int bx, int j) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    const int i = blockIdx.x * 256 + threadIdx.x * 4, j = blockIdx.y;
+    const int i = bx * 256 + threadIdx.x * 4;
     const size_t o = (size_t)j * cx.m_pad + i;
     const float4 acc = gemm_out4(src, i, j);
     const float4 c1 = cx.c1 ? __ldcg(reinterpret_cast<const float4*>(cx.c1 + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -196,6 +196,13 @@ __global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void*
     }
 }
 
+template <bool BF16>
+__global__ void __launch_bounds__(64) k_reduce_rhs(IterCtx cx, SumSrc src, void* rhs, float* rhs32) {
+    pdl_trigger();
+    pdl_wait();
+    reduce_rhs_body<BF16>(cx, src, rhs, rhs32, blockIdx.x, blockIdx.y);
+}
+
 __device__ inline void split3_store(const float v[4], __nv_bfloat16* d, size_t plane) {
     __nv_bfloat16 hi[4], mid[4], lo[4];
 #pragma unroll
@@ -217,18 +224,23 @@ __device__ inline void split3_store(const float v[4], __nv_bfloat16* d, size_t p
 // (refine_on = 0: refine_after, the column is younger than the limit) gets
 // e = 0, so its correction S^{-1} e is exactly zero and its v is bitwise the
 // unrefined solve's.  Grid (m_pad / 256, Kp), 64 threads.
-__global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const float* __restrict__ rhs32,
-                                                   __nv_bfloat16* rhs) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void reduce_err_body(const IterCtx& cx, const SumSrc& src, const float* rhs32,
+                                                __nv_bfloat16* rhs, int bx, int j) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    const int i = blockIdx.x * 256 + threadIdx.x * 4, j = blockIdx.y;
+    const int i = bx * 256 + threadIdx.x * 4;
     const size_t o = (size_t)j * cx.m_pad + i;
     const float4 sv = gemm_out4(src, i, j);
     const float4 b = *reinterpret_cast<const float4*>(rhs32 + o);
     float e[4] = {b.x - sv.x, b.y - sv.y, b.z - sv.z, b.w - sv.w};
     if (cx.refine_on[j] == 0.f) e[0] = e[1] = e[2] = e[3] = 0.f;
     split3_store(e, rhs + o, (size_t)cx.Kp * cx.m_pad);
+}
+
+__global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const float* __restrict__ rhs32,
+                                                   __nv_bfloat16* rhs) {
+    pdl_trigger();
+    pdl_wait();
+    reduce_err_body(cx, src, rhs32, rhs, blockIdx.x, blockIdx.y);
 }
 
 // v = S^{-1} rhs;  q2' = v + P2(q2);  residual partials of the m-block (one
@@ -243,13 +255,11 @@ __global__ void __launch_bounds__(64) k_reduce_err(IterCtx cx, SumSrc src, const
 enum { RS_PLAIN = 0, RS_FIRST = 1, RS_FINAL = 2, RS_ACCUM = 3 };
 
 template <bool BF16, int MODE>
-__global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, void* V, float* rv,
-                                                     __nv_bfloat16* V3) {
-    pdl_trigger();
-    pdl_wait();
+__device__ __forceinline__ void reduce_solve_body(const IterCtx& cx, const SumSrc& src, void* V, float* rv,
+                                                  __nv_bfloat16* V3, int bx, int j) {
     if (cx.ctrl->n_active == 0 || cx.ctrl->err) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, j = blockIdx.y;
-    const int rt = blockIdx.x * 2 + w, i = rt * 128 + lane * 4;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rt = bx * 2 + w, i = rt * 128 + lane * 4;
     const size_t o = (size_t)j * cx.m_pad + i;
     float4 v = gemm_out4(src, i, j);
     if (MODE == RS_ACCUM || MODE == RS_FINAL) {
@@ -296,6 +306,14 @@ __global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, voi
     }
 }
 
+template <bool BF16, int MODE>
+__global__ void __launch_bounds__(64) k_reduce_solve(IterCtx cx, SumSrc src, void* V, float* rv,
+                                                     __nv_bfloat16* V3) {
+    pdl_trigger();
+    pdl_wait();
+    reduce_solve_body<BF16, MODE>(cx, src, V, rv, V3, blockIdx.x, blockIdx.y);
+}
+
 // q1' = P1(q1) - c/rho - W and R1' = 2 P1(q1') - q1' - c/rho from W = A^T V;
 // residual partials of the n-block (one per 128-row block and column).  The
 // FP32 form's step after its cuBLAS GEMM2 (the BF16 forms run it in the
@@ -328,14 +346,11 @@ __global__ void __launch_bounds__(128) k_q1_update(IterCtx cx, SumSrc src, void*
     }
 }
 
-// Per-column stop test and bookkeeping; the last kernel of an iteration whose
-// GEMM2 does not do it itself (residual-test iterations, the FP32 form,
-// groups).  One block per column sums that column's residual partials (fixed
-// order, deterministic); the last block to finish (ticket) updates the
-// control block.
-__global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
-    pdl_trigger();
-    pdl_wait();
+// Per-column stop test and bookkeeping; the last kernel of every iteration.
+// One block per column sums that column's residual partials (fixed order,
+// deterministic); the last block to finish (ticket) updates the control
+// block.
+__device__ __forceinline__ void finalize_body(const IterCtx& cx) {
     Control* c = cx.ctrl;
     if (c->n_active == 0) return;
     const int it = c->iter + 1;
@@ -345,13 +360,72 @@ __global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(&c->ticket, 1) == (int)gridDim.x - 1;
+        last = atomicAdd(&c->ticket, 1) == cx.Kp - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     __shared__ int cnt;
     finalize_count(cx, it, &cnt);
+}
+
+__global__ void __launch_bounds__(128) k_finalize(IterCtx cx) {
+    pdl_trigger();
+    pdl_wait();
+    finalize_body(cx);
+}
+
+// The element-wise kernels over the members of a group solve (run_group):
+// one launch per step, member g = blockIdx.z, each member's own grid inside
+// the launch's (the largest member's); the bodies are those above.
+struct EwMember {
+    IterCtx cx;
+    SumSrc src;
+    void* p0;               // rhs planes (reduce_rhs), V (reduce_solve), rhs planes (reduce_err)
+    float* f1;              // rhs32 (reduce_rhs, reduce_err), rv (reduce_solve)
+    __nv_bfloat16* b2;      // V3 (reduce_solve)
+};
+struct EwGroup {
+    EwMember m[4];
+    int G;
+};
+
+__device__ __forceinline__ const EwMember* ew_member(const EwGroup& P, int rows_per_block) {
+    if ((int)blockIdx.z >= P.G) return nullptr;
+    const EwMember& e = P.m[blockIdx.z];
+    if ((int)blockIdx.x >= e.cx.m_pad / rows_per_block || (int)blockIdx.y >= e.cx.Kp) return nullptr;
+    return &e;
+}
+
+__global__ void __launch_bounds__(64) k_reduce_rhs_g(const __grid_constant__ EwGroup P) {
+    pdl_trigger();
+    pdl_wait();
+    if (const EwMember* e = ew_member(P, 256))
+        reduce_rhs_body<true>(e->cx, e->src, e->p0, e->f1, blockIdx.x, blockIdx.y);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(64) k_reduce_solve_g(const __grid_constant__ EwGroup P) {
+    pdl_trigger();
+    pdl_wait();
+    if (const EwMember* e = ew_member(P, 256))
+        reduce_solve_body<true, MODE>(e->cx, e->src, e->p0, e->f1, e->b2, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(64) k_reduce_err_g(const __grid_constant__ EwGroup P) {
+    pdl_trigger();
+    pdl_wait();
+    if (const EwMember* e = ew_member(P, 256))
+        reduce_err_body(e->cx, e->src, e->f1, static_cast<__nv_bfloat16*>(e->p0), blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(128) k_finalize_g(const __grid_constant__ EwGroup P) {
+    pdl_trigger();
+    pdl_wait();
+    if ((int)blockIdx.z >= P.G) return;
+    const EwMember& e = P.m[blockIdx.z];
+    if ((int)blockIdx.x >= e.cx.Kp) return;
+    finalize_body(e.cx);
 }
 
 // c^T z1 in FP64 per column (deterministic block reduction).
@@ -624,16 +698,10 @@ static int iteration_bf16(ResultData& r, const IterCtx& cx, int itx) {
     if (full && (rc = tc_gemm2_lo(r, pdl, first_only))) return rc;
     ran(full);
     next();
-    // between residual tests the finalize step (iteration counters, the
-    // iteration cap) runs in GEMM2's last CTA instead of its own kernel
-    const bool fold = !test_slot;
-    if ((rc = tc_gemm2(r, pdl, fold))) return rc;
+    if ((rc = tc_gemm2(r, pdl))) return rc;
     next();
-    if (!fold) {
-        LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
-        LGK_LAUNCH_CHECK();
-    }
-    ran(!fold);
+    LGK_CUDA_TRY(launch_k(k_finalize, dim3(r.Kp), dim3(128), 0, st, pdl, cx));
+    LGK_LAUNCH_CHECK();
     next();
     return LGK_OK;
 }
@@ -831,16 +899,21 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
         std::lock_guard<std::mutex> lk(cs.tune_mu);
         auto it = cs.tuned.find(Kp);
         if (it != cs.tuned.end()) {
-            r.force_wide = it->second.first;
+            r.force_wide = it->second.first & 1;
+            r.force_wide2 = (it->second.first >> 1) & 1;
             r.n_tile_s = it->second.second;
         } else {
+            // candidates: 256- or 128-row tiles for GEMM1 (bit 0) and for
+            // GEMM2 (bit 1) where the one-term A operand allows them, x the
+            // solve's column tile whole or halved; the first is the default
             const bool can_wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
-            std::vector<int> ws = can_wide ? std::vector<int>{1, 0} : std::vector<int>{0};
+            std::vector<int> ws = can_wide ? std::vector<int>{3, 1, 2, 0} : std::vector<int>{0};
             std::vector<int> ss{r.n_tile_s};
             if (r.n_tile_s % 32 == 0) ss.push_back(r.n_tile_s / 2);
             for (int w : ws)
                 for (int t : ss) cands.push_back({w, t});
-            r.force_wide = cands[0].first;
+            r.force_wide = cands[0].first & 1;
+            r.force_wide2 = (cands[0].first >> 1) & 1;
             r.n_tile_s = cands[0].second;
         }
     }
@@ -1178,7 +1251,8 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
     auto reconfigure = [&](int wide, int nts) -> int {
         cudaGraphExecDestroy(r.graph);
         r.graph = nullptr;
-        r.force_wide = wide;
+        r.force_wide = wide & 1;
+        r.force_wide2 = (wide >> 1) & 1;
         r.n_tile_s = nts;
         int rc2 = tc_prepare(r);
         if (rc2) return rc2;
@@ -1268,7 +1342,7 @@ int run_solve(ResultData& r, const double* W, const double* rho, const double* q
                 std::lock_guard<std::mutex> lk(cs.tune_mu);
                 cs.tuned[Kp] = pick;
             }
-            if ((pick.first != r.force_wide || pick.second != r.n_tile_s) &&
+            if ((pick.first != (r.force_wide | (r.force_wide2 << 1)) || pick.second != r.n_tile_s) &&
                 (rc = reconfigure(pick.first, pick.second)))
                 break;
         }
@@ -1337,8 +1411,8 @@ static int fail_status(int code, const std::string& msg) {
 }
 
 // One iteration of a group (the sequence of iteration_bf16): every tensor-core
-// product is one launch over all G solves; the element-wise kernels run per
-// solve, back to back on the group's stream.
+// product is one launch over all G solves, and so is every element-wise step
+// (member = blockIdx.z), on the group's stream.
 static int iteration_group(int G, ResultData* const* R, const IterCtx* cx, cudaStream_t st, int itx) {
     const ResultData& r0 = *R[0];
     const int check_every = r0.cs->prm.check_every;
@@ -1346,58 +1420,71 @@ static int iteration_group(int G, ResultData* const* R, const IterCtx* cx, cudaS
     const bool full = r0.refine && (itx == 0 || test_slot);
     const bool first_only = itx == 0 && !test_slot;
     const bool pdl = true;
+    const int steps = r0.refine_steps;
+    int mx = 1, kx = 1;
+    for (int g = 0; g < G; ++g) {
+        mx = std::max(mx, R[g]->cs->m_pad / 256);
+        kx = std::max(kx, R[g]->Kp);
+    }
+    const dim3 gm(mx, kx, G);
+    // the members' arguments of one element-wise step
+    auto ew = [&](auto fill) {
+        EwGroup P;
+        memset(&P, 0, sizeof(P));
+        P.G = G;
+        for (int g = 0; g < G; ++g) {
+            P.m[g].cx = cx[g];
+            fill(*R[g], P.m[g]);
+        }
+        return P;
+    };
     int rc;
     if (full && (rc = tc_group_gemm1_lo(G, R, st, pdl && itx > 0, first_only))) return rc;
     if ((rc = tc_group_gemm1(G, R, st, pdl && (itx > 0 || full)))) return rc;
-    for (int g = 0; g < G; ++g) {
-        ResultData& r = *R[g];
-        const dim3 gm(r.cs->m_pad / 256, r.Kp);
-        float* rhs32 = r.refine_steps ? r.rhs32.as<float>() : nullptr;
-        LGK_CUDA_TRY(launch_k(k_reduce_rhs<true>, gm, dim3(64), 0, st, pdl, cx[g], plan_src(r, r.plan1), r.rhs.p,
-                              rhs32));
+    {
+        EwGroup P = ew([&](ResultData& r, EwMember& m) {
+            m.src = plan_src(r, r.plan1);
+            m.p0 = r.rhs.p;
+            m.f1 = steps ? r.rhs32.as<float>() : nullptr;
+        });
+        LGK_CUDA_TRY(launch_k(k_reduce_rhs_g, gm, dim3(64), 0, st, pdl, P));
         LGK_LAUNCH_CHECK();
     }
     if ((rc = tc_group_solve(G, R, st, pdl))) return rc;
-    const int steps = r0.refine_steps;
-    for (int g = 0; g < G; ++g) {
-        ResultData& r = *R[g];
-        const dim3 gm(r.cs->m_pad / 256, r.Kp);
-        __nv_bfloat16* V3 = steps ? r.V3.as<__nv_bfloat16>() : nullptr;
-        float* rv = steps ? r.rv.as<float>() : nullptr;
-        if (steps == 0)
-            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_PLAIN>, gm, dim3(64), 0, st, pdl, cx[g],
-                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
-        else
-            LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FIRST>, gm, dim3(64), 0, st, pdl, cx[g],
-                                  plan_src(r, r.plan_s), r.V.p, rv, V3));
+    auto solve_args = [&](ResultData& r, EwMember& m) {
+        m.src = plan_src(r, r.plan_s);
+        m.p0 = r.V.p;
+        m.f1 = steps ? r.rv.as<float>() : nullptr;
+        m.b2 = steps ? r.V3.as<__nv_bfloat16>() : nullptr;
+    };
+    {
+        EwGroup P = ew(solve_args);
+        if (steps == 0) LGK_CUDA_TRY(launch_k(k_reduce_solve_g<RS_PLAIN>, gm, dim3(64), 0, st, pdl, P));
+        else LGK_CUDA_TRY(launch_k(k_reduce_solve_g<RS_FIRST>, gm, dim3(64), 0, st, pdl, P));
         LGK_LAUNCH_CHECK();
     }
     for (int step = 1; step <= steps; ++step) {
         if ((rc = tc_group_sv(G, R, st, pdl))) return rc;
-        for (int g = 0; g < G; ++g) {
-            ResultData& r = *R[g];
-            const dim3 gm(r.cs->m_pad / 256, r.Kp);
-            LGK_CUDA_TRY(launch_k(k_reduce_err, gm, dim3(64), 0, st, pdl, cx[g], plan_src(r, r.plan_s),
-                                  r.rhs32.as<float>(), r.rhs.as<__nv_bfloat16>()));
+        {
+            EwGroup P = ew([&](ResultData& r, EwMember& m) {
+                m.src = plan_src(r, r.plan_s);
+                m.p0 = r.rhs.p;
+                m.f1 = r.rhs32.as<float>();
+            });
+            LGK_CUDA_TRY(launch_k(k_reduce_err_g, gm, dim3(64), 0, st, pdl, P));
             LGK_LAUNCH_CHECK();
         }
         if ((rc = tc_group_solve(G, R, st, pdl))) return rc;
-        for (int g = 0; g < G; ++g) {
-            ResultData& r = *R[g];
-            const dim3 gm(r.cs->m_pad / 256, r.Kp);
-            if (step < steps)
-                LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_ACCUM>, gm, dim3(64), 0, st, pdl, cx[g],
-                                      plan_src(r, r.plan_s), r.V.p, r.rv.as<float>(), r.V3.as<__nv_bfloat16>()));
-            else
-                LGK_CUDA_TRY(launch_k(k_reduce_solve<true, RS_FINAL>, gm, dim3(64), 0, st, pdl, cx[g],
-                                      plan_src(r, r.plan_s), r.V.p, r.rv.as<float>(), r.V3.as<__nv_bfloat16>()));
-            LGK_LAUNCH_CHECK();
-        }
+        EwGroup P = ew(solve_args);
+        if (step < steps) LGK_CUDA_TRY(launch_k(k_reduce_solve_g<RS_ACCUM>, gm, dim3(64), 0, st, pdl, P));
+        else LGK_CUDA_TRY(launch_k(k_reduce_solve_g<RS_FINAL>, gm, dim3(64), 0, st, pdl, P));
+        LGK_LAUNCH_CHECK();
     }
     if (full && (rc = tc_group_gemm2_lo(G, R, st, pdl, first_only))) return rc;
     if ((rc = tc_group_gemm2(G, R, st, pdl))) return rc;
-    for (int g = 0; g < G; ++g) {
-        LGK_CUDA_TRY(launch_k(k_finalize, dim3(R[g]->Kp), dim3(128), 0, st, pdl, cx[g]));
+    {
+        EwGroup P = ew([&](ResultData&, EwMember&) {});
+        LGK_CUDA_TRY(launch_k(k_finalize_g, dim3(kx, 1, G), dim3(128), 0, st, pdl, P));
         LGK_LAUNCH_CHECK();
     }
     return LGK_OK;
@@ -1419,12 +1506,17 @@ int run_group(int G, ResultData* const* R) {
                                            "low term, solve refinement, residual-test spacing)");
     }
     int rc;
-    // one tile height for all: 256-row tiles only if every solve can take them
-    bool all_wide = true;
-    for (int g = 0; g < G; ++g) all_wide = all_wide && R[g]->wide;
+    // one tile height per GEMM for all: 256-row tiles only if every solve can
+    // take them
+    bool all_wide = true, all_wide2 = true;
+    for (int g = 0; g < G; ++g) {
+        all_wide = all_wide && R[g]->wide;
+        all_wide2 = all_wide2 && R[g]->wide2;
+    }
     for (int g = 0; g < G; ++g)
-        if (R[g]->wide != all_wide) {
-            R[g]->force_wide = 0;
+        if (R[g]->wide != all_wide || R[g]->wide2 != all_wide2) {
+            R[g]->force_wide = all_wide ? 1 : 0;
+            R[g]->force_wide2 = all_wide2 ? 1 : 0;
             if ((rc = tc_prepare(*R[g]))) return rc;
         }
     cudaStream_t st = c0.stream;

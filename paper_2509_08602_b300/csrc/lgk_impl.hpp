@@ -66,7 +66,8 @@ struct CaseData {
     std::atomic<int> async_busy{0};   // an asynchronous solve of this case is running
     std::unique_ptr<CheckTC> chk_tc;  // plans, maps and buffers of the plan check, made on first use
     // GEMM configurations chosen by the autotuner (lgk_params.autotune), per
-    // column count Kp: (256-row tiles for the A GEMMs, solve column tile)
+    // column count Kp: (256-row tiles for GEMM1 in bit 0 and for GEMM2 in
+    // bit 1, solve column tile)
     std::map<int, std::pair<int, int>> tuned;
     std::mutex tune_mu;
     size_t bytes_held() const;
@@ -125,6 +126,8 @@ struct ResultData {
     bool refine = false;      // lo_refresh: heavy products with A_hi, lo products lagged
     bool wide = false;        // GEMM1 / GEMM2 (and the lo products) on 256-row tiles
     int force_wide = -1;      // autotuner: -1 the default rule, 0 / 1 forced (where allowed)
+    bool wide2 = false;       // GEMM2 (and its low-term product) on 256-row tiles
+    int force_wide2 = -1;     // autotuner / group: -1 lgk_params.gemm2_tile_rows, 0 / 1 forced
     DevBuf c1, c2;            // float [Kp][m_pad] lo R1_hi, [Kp][n_pad] lo^T V_hi (last full iteration)
     int refine_steps = 0;     // solve refinement steps per iteration (lgk_params.solve_refine)
     bool l2_keep = false;     // l2_keep_inverse: the solve's S^{-1} loads persist in an L2 carve-out
@@ -255,9 +258,7 @@ int tc_gemm1_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_gemm2_lo(ResultData& r, bool pdl = false, bool first_only = false);
 int tc_solve(ResultData& r, bool pdl = false);     // part[s] = G3 . rhs^T  (6 products)
 int tc_sv(ResultData& r, bool pdl = false);        // part[s] = S3 . V3^T   (6 products, refinement)
-// fused: q1, R1 update from Ahat^T . V; fold: the kernel also runs the
-// iteration's finalize step (stop tests, counters) in its last CTA
-int tc_gemm2(ResultData& r, bool pdl = false, bool fold = false);
+int tc_gemm2(ResultData& r, bool pdl = false);     // fused: q1, R1 update from Ahat^T . V
 // the same products over a group of solves, one launch each, on stream st
 int tc_group_gemm1(int G, ResultData* const* R, cudaStream_t st, bool pdl);
 int tc_group_gemm1_lo(int G, ResultData* const* R, cudaStream_t st, bool pdl, bool first_only);

@@ -73,8 +73,6 @@ struct TcArgs {
     int first_only;         // do the work only in the solve's first iteration (else return)
     int keep_a;             // load A with an evict-last L2 policy (S^{-1} kept in L2 across iterations)
     int ncta;               // CTAs with a run in this case's plan (the rest skip the case)
-    int fold_finalize;      // EPI_Q1, one case: the last CTA to finish runs the iteration's
-                            // finalize step (stop tests, counters) instead of a separate kernel
     float* part;            // [slot][n_tile][128] partial sums of tiles split over segments
     void* out;              // EPI_STORE: float [Kp][out_ld];
                             // EPI_Q1: R1 [2][Kp][n_pad] (BF16 terms)
@@ -257,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 8);
     int* sh_last = reinterpret_cast<int*>(bars + 2 * S + 8) + 1;
     int* sh_run = reinterpret_cast<int*>(bars + 2 * S + 9);         // bit g: case g has work
+    int* sh_pre = sh_run + 1;                                       // stages prefetched for case 0
     float* red = reinterpret_cast<float*>(bars + 2 * S + 10);       // [8 warps][kChunk][5]
     const int NBUF = a0.nbuf;
     const int TC = a0.tmem_cols;                                    // columns of one accumulator
@@ -279,11 +278,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     // tail.  Their bytes are added to the stage's full barrier as a pending
     // transaction without an arrival: the stage cannot complete before the
     // arrival that comes with its B tile, after the wait.  (Not for launches
-    // that work only in the solve's first iteration: they mostly do nothing;
-    // not for groups.)
+    // that work only in the solve's first iteration: they mostly do nothing.)
+    // In a group, for case 0.
     const uint32_t a_bytes = (uint32_t)(NA * MT * kABytes);
     int pre = 0;
-    if (G == 1 && !a0.first_only && warp == 0 && lane == 0 && (int)blockIdx.x < a0.ncta) {
+    if (!a0.first_only && warp == 0 && lane == 0 && (int)blockIdx.x < a0.ncta) {
         const int s0 = a0.cta_seg[blockIdx.x], s1 = a0.cta_seg[blockIdx.x + 1];
         prefetch_tmap(&P.tmA[0]);
         prefetch_tmap(&P.tmB[0]);
@@ -309,23 +308,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
                 m |= 1 << g;
         }
         *sh_run = m;
+        *sh_pre = pre;                                  // thread 0 is the producer
     }
     __syncthreads();
     const int runmask = *sh_run;
+    // stages prefetched for case 0 when case 0 has stopped (or an error is
+    // pending): the producer lets them land and both pipelines start after them
+    const int skip = (runmask & 1) ? 0 : *sh_pre;
 
     if (warp == 0 && lane == 0) {
         int* err = &P.cx[0].ctrl->err;
-        if (pre > 0 && !(runmask & 1)) {
-            // the one case has stopped (or an error is pending): nothing to do
-            // but let the prefetched A tiles land (bounded) before the CTA exits
-            for (int s = 0; s < pre; ++s) {
-                mbar_arrive(smem_u32(&bars[s]));
-                mbar_wait(smem_u32(&bars[s]), 0u, err);
-            }
+        for (int s = 0; s < skip; ++s) {
+            mbar_arrive(smem_u32(&bars[s]));
+            mbar_wait(smem_u32(&bars[s]), 0u, err);
         }
         // ---------------- TMA producer: one continuous stream of k blocks
         bool ok = true;
-        int it = 0;
+        int it = skip;
         // A streams through once per launch; the B operand, S^{-1} and the
         // epilogue's state should outlive it in L2
         const uint64_t pol_a = a0.keep_a ? policy_evict_last() : policy_evict_first();
@@ -367,7 +366,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         bool ok = true;
-        int it = 0, u = 0;
+        int it = skip, u = 0;
+        for (int s = 0; s < skip; ++s) mbar_arrive(smem_u32(&bars[S + s]));   // skipped stages are free
 #pragma unroll
         for (int gi = 0; gi < kMaxGroup; ++gi) {
             if (gi >= G) break;
@@ -533,33 +533,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, NBUF * MT * TC);
-    }
-    if (EPI == EPI_Q1 && a0.fold_finalize) {
-        // the iteration's finalize step in the last CTA to finish (every
-        // CTA's epilogue stores are fenced before its ticket)
-        const IterCtx& cx = P.cx[0];
-        Control* c = cx.ctrl;
-        if (threadIdx.x == 0) {
-            __threadfence();
-            *sh_last = atomicAdd(&c->ticket, 1) == (int)gridDim.x - 1;
-        }
-        __syncthreads();
-        if (*sh_last) {
-            __threadfence();
-            if (c->n_active != 0) {
-                const int it = c->iter + 1;
-                const bool er = c->err != 0;
-                double* redd = reinterpret_cast<double*>(red);      // 5 x 10 doubles
-                for (int j = 0; j < cx.Kp; ++j) {
-                    finalize_column(cx, j, it, er, redd);
-                    __syncthreads();
-                }
-                __threadfence();
-                finalize_count(cx, it, sh_run);
-            } else if (threadIdx.x == 0) {
-                c->ticket = 0;
-            }
-        }
     }
 }
 
@@ -753,7 +726,7 @@ static size_t group_layout(TcGroup& g, bool first_only, bool keep_a) {
 
 template <int NA, int NB, int NT, bool A_MN, int EPI, int MT = 1>
 static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& P, ResultData& r,
-                  void* out, bool pdl, bool first_only = false, bool keep_a = false, bool fold = false) {
+                  void* out, bool pdl, bool first_only = false, bool keep_a = false) {
     if (P.mt != MT) {
         set_error("tensor-core GEMM: plan built for another tile height");
         return LGK_EINVAL;
@@ -768,7 +741,6 @@ static int launch(const CUtensorMap& mA, const CUtensorMap& mB, const GemmPlan& 
     const bool keep = keep_a && r.l2_keep;
     const size_t smem = group_layout<NA, NB, MT>(g, first_only, keep);
     if (!smem) return LGK_EINVAL;
-    g.a[0].fold_finalize = EPI == EPI_Q1 && fold;
     LGK_CUDA_TRY(launch_k_win(k_tc_gemm<NA, NB, NT, A_MN, EPI, MT>, dim3(P.grid), dim3(kThreads), smem,
                               r.cs->stream, pdl, keep ? &r.l2win : nullptr, g));
     LGK_LAUNCH_CHECK();
@@ -863,13 +835,18 @@ int tc_prepare(ResultData& r) {
     // fit in tensor memory next to each other
     const bool can_wide = (cs.na == 1 || r.refine) && r.n_tile <= 128;
     r.wide = can_wide && (r.force_wide < 0 || r.force_wide == 1);
-    const int hm = r.wide ? 2 : 1;
+    // GEMM2's tile height: lgk_params.gemm2_tile_rows (0: as GEMM1), unless
+    // the autotuner or a group forces one
+    const int p2 = cs.prm.gemm2_tile_rows;
+    r.wide2 = r.force_wide2 >= 0 ? can_wide && r.force_wide2 == 1
+                                 : (p2 == 128 ? false : p2 == 256 ? can_wide : r.wide);
+    const int hm = r.wide ? 2 : 1, hm2 = r.wide2 ? 2 : 1;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
     if ((rc = build_plan(r.plan1, mt / hm, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false, hm))) return rc;
     if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s, false, 1))) return rc;
-    if ((rc = build_plan(r.plan2, nt / hm, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true, hm))) return rc;
+    if ((rc = build_plan(r.plan2, nt / hm2, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true, hm2))) return rc;
     size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile * hm, (size_t)r.plan_s.nseg * r.n_tile_s,
-                             (size_t)r.plan2.nseg * r.n_tile * hm});
+                             (size_t)r.plan2.nseg * r.n_tile * hm2});
     return r.part.alloc(slots * 128 * 4);
 }
 
@@ -936,12 +913,10 @@ int tc_sv(ResultData& r, bool pdl) {
     return launch<3, 3, 6, false, EPI_PARTIAL>(r.maps.S3, r.maps.V3, r.plan_s, r, nullptr, pdl);
 }
 
-int tc_gemm2(ResultData& r, bool pdl, bool fold) {
-    if (r.cs->na == 2 && !r.refine)
-        return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
-    if (r.plan2.mt == 2)
-        return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
-    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl, false, false, fold);
+int tc_gemm2(ResultData& r, bool pdl) {
+    if (r.cs->na == 2 && !r.refine) return launch<2, 2, 3, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    if (r.plan2.mt == 2) return launch<1, 2, 2, true, EPI_Q1, 2>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
+    return launch<1, 2, 2, true, EPI_Q1>(r.maps.A_mn, r.maps.V, r.plan2, r, r.R1.p, pdl);
 }
 
 }  // namespace lgk

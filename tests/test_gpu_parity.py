@@ -520,7 +520,7 @@ def test_tensor_core_schur_complement_matches_fp64(lgk, cfg0, prec):
 def test_autotuned_solve(lgk, cfg0):
     """lgk_params.autotune: the first solve of a case at 32 columns (lagged
     two-term form) times each GEMM configuration on one replay of the real
-    iteration (256- or 128-row tiles for the A GEMMs x the solve's column
+    iteration (256- or 128-row tiles for GEMM1 and for GEMM2 x the solve's column
     tile whole or halved) and keeps the fastest for the case.  Later solves
     at that width start with it: two of them agree bit for bit.  The tuned
     plans meet the same converged gates as untuned ones (objective within
