@@ -442,6 +442,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
                 const int row = (rt * MT + hrow) * 128 + r, col0 = ct * a.n_tile;
                 double* rdst = cx.resid +
                                ((size_t)(rt * MT + hrow) * cx.Kp + col0) * 5;
+                // a whole tile of the q1 step: the state of its first two
+                // chunks is loaded before the wait for the accumulator, so the
+                // loads are in flight while the tile's k loop still runs (the
+                // epilogue of a CTA's last tile is otherwise exposed).  Only
+                // this epilogue writes these rows of q1 in this launch.
+                Q1In inA, inB;
+                if (EPI == EPI_Q1 && se - sb == 1) {
+                    q1_load(cx, row, col0 + cbeg, inA);
+                    if (cbeg + kChunk < cend) q1_load(cx, row, col0 + cbeg + kChunk, inB);
+                }
                 if (ok) ok = mbar_wait(smem_u32(&bars[2 * S + b]), (uint32_t)((u / NBUF) & 1), err);
                 tc_fence_after();
                 const uint32_t base =
@@ -484,16 +494,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
                         epi_bar();
                     }
                 } else if (EPI == EPI_Q1) {
-                    // the whole k range of the tile is in this accumulator; the
-                    // next chunk's inputs load while this one is finished
-                    // (two named buffers, unrolled by two, so both stay in registers)
-                    Q1In inA, inB;
+                    // the whole k range of the tile is in this accumulator; two
+                    // chunks' inputs are in flight while one is finished (two
+                    // named buffers, unrolled by two, so both stay in registers)
                     float vA[kChunk], vB[kChunk], res[kChunk][5];
-                    q1_load(cx, row, col0 + cbeg, inA);
                     tmem_ld8(base + (uint32_t)cbeg, vA);
                     for (int c0 = cbeg; c0 < cend; c0 += 2 * kChunk) {
                         const bool moreB = c0 + kChunk < cend;
-                        if (moreB) q1_load(cx, row, col0 + c0 + kChunk, inB);
                         if (!ok)
                             for (int c = 0; c < kChunk; ++c) vA[c] = 0.f;
                         q1_finish(cx, a, row, col0 + c0, vA, inA, res);
@@ -506,6 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
                             for (int c = 0; c < kChunk; ++c) vB[c] = 0.f;
                         q1_finish(cx, a, row, col0 + c0 + kChunk, vB, inB, res);
                         if (check) epi_resid(res, red, rdst + (c0 + kChunk) * 5, lane, ew, hf, et);
+                        if (c0 + 3 * kChunk < cend) q1_load(cx, row, col0 + c0 + 3 * kChunk, inB);
                         if (moreA) tmem_ld8(base + (uint32_t)(c0 + 2 * kChunk), vA);
                     }
                     tc_fence_before();

@@ -13,11 +13,15 @@ between it and c^T z1), and stores them as JSON.
 
     python tests/golden/make_full_size.py --cfg 1     # about 30 min on 4 host cores
     python tests/golden/make_full_size.py --cfg 2     # about 1-2 h (each iteration streams A)
+    python tests/golden/make_full_size.py --cfg 3     # hours (A is 8.2 GB in FP64)
 
 The sampled weightings (indices into `synth.cases.slider_weights(grid)`,
-row-major over (s_LD, s_BOT)) are the four corners of the slider grid, its
-centre and one off-centre point; index 0 (s_LD = s_BOT = 0, the lowest BOT
-weight) converges slowest.
+row-major over (s_LD, s_BOT)) are, for cfg 1 and 2, the four corners of the
+slider grid, its centre and one off-centre point; index 0 (s_LD = s_BOT = 0,
+the lowest BOT weight) converges slowest.  For the 9-target cfg 3 case the
+lowest BOT weights take over 10^4 iterations, hours per weighting for the
+FP64 oracle on the host, so its sample is four weightings of the upper half
+of the BOT slider: the two top corners, the centre and one point between.
 """
 from __future__ import annotations
 
@@ -39,12 +43,14 @@ from oracle import metrics as M        # noqa: E402
 from synth import cases as SC          # noqa: E402
 
 TOL = 5e-5
-GRID_SPACING = {1: 2.0, 2: 2.0}        # mm
+GRID_SPACING = {1: 2.0, 2: 2.0, 3: 2.0}    # mm
 GRID_MARGIN = 12.0                     # mm
 
 
-def sample_indices(g: int) -> list[int]:
+def sample_indices(g: int, cfg: int = 1) -> list[int]:
     c = g // 2
+    if cfg == 3:            # upper half of the BOT slider (index = s_LD row * g + s_BOT column)
+        return sorted({g - 1, g * g - 1, c * g + c, (c // 2) * g + (c + g) // 2})
     return sorted({0, g - 1, g * (g - 1), g * g - 1, c * g + c, (c // 2) * g + c // 2})
 
 
@@ -77,7 +83,7 @@ def run_chunked(lp, b, l, u, rho, max_iter, t0, chunk=2000):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--cfg", type=int, required=True, choices=(1, 2))
+    ap.add_argument("--cfg", type=int, required=True, choices=(1, 2, 3))
     ap.add_argument("--max-iter", type=int, default=40000)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
@@ -86,7 +92,7 @@ def main():
     t0 = time.time()
     case = SC.workload_case(a.cfg)
     g = SC.WORKLOADS[a.cfg]["grid"]
-    idx = sample_indices(g)
+    idx = sample_indices(g, a.cfg)
     W = SC.slider_weights(g)[idx]
     lp = L.precondition(L.assemble_case(case))
     rho0 = L.rho0_for(lp)
