@@ -238,8 +238,12 @@ int lgk_solve_weightings(lgk_case* cs, int K, const double* W, const double* rho
  * with its own control block and stop test; every case's products are cut
  * into the same stream-K runs and summed in the same order as in a solve of
  * that case alone, so each result is bitwise that of lgk_solve_weightings
- * with the same arguments (except that the long-solve switches
- * lo_refresh_iters and refine_after do not apply, and autotune is ignored).
+ * with the same arguments, as long as the group runs on the tile heights the
+ * case would take alone (256-row tiles need every case to allow them) and no
+ * other member reaches lo_refresh_iters first: once the oldest running member
+ * passes lo_refresh_iters, the whole group continues with the literal
+ * iteration.  refine_after does not apply in a group, and autotune is
+ * ignored.
  *   cases: G distinct cases on one device; all BF16 forms with the same
  *          lo_refresh, solve_refine and check_every (else LGK_EINVAL).
  *   K, W, rho: per case, as in lgk_solve_weightings (rho may be NULL, or

@@ -1523,35 +1523,44 @@ int run_group(int G, ResultData* const* R) {
     const int per_graph = std::max(1, std::min(r0.max_iter, 5 * c0.prm.check_every));
     std::vector<IterCtx> cx(G);
     for (int g = 0; g < G; ++g) cx[g] = make_ctx(*R[g]);
-    // the group's graph of per_graph iterations
-    cudaGraph_t graph = nullptr;
+    // the group's graph of per_graph iterations (captured again when the
+    // group changes its iteration form)
     cudaGraphExec_t exec = nullptr;
-    LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    for (int it = 0; it < per_graph; ++it) {
-        if ((rc = iteration_group(G, R, cx.data(), st, it))) {
-            cudaStreamEndCapture(st, &graph);
-            if (graph) cudaGraphDestroy(graph);
-            return rc;
-        }
-    }
-    LGK_CUDA_TRY(cudaStreamEndCapture(st, &graph));
-    size_t n_all = 0, n_nodes = 0;
-    if (cudaGraphGetNodes(graph, nullptr, &n_all) == cudaSuccess && n_all) {
-        std::vector<cudaGraphNode_t> nodes(n_all);
-        if (cudaGraphGetNodes(graph, nodes.data(), &n_all) == cudaSuccess)
-            for (auto nd : nodes) {
-                cudaGraphNodeType ty;
-                if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
-            }
-    }
-    count_launch(-(long long)n_nodes);
-    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) return fail_status(LGK_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
     struct ExecGuard {
-        cudaGraphExec_t e;
-        ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
-    } guard{exec};
+        cudaGraphExec_t* e;
+        ~ExecGuard() { if (*e) cudaGraphExecDestroy(*e); }
+    } guard{&exec};
+    size_t n_nodes = 0;
+    auto capture = [&]() -> int {
+        cudaGraph_t graph = nullptr;
+        LGK_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < per_graph; ++it) {
+            const int rc2 = iteration_group(G, R, cx.data(), st, it);
+            if (rc2) {
+                cudaStreamEndCapture(st, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                return rc2;
+            }
+        }
+        LGK_CUDA_TRY(cudaStreamEndCapture(st, &graph));
+        size_t n_all = 0;
+        n_nodes = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &n_all) == cudaSuccess && n_all) {
+            std::vector<cudaGraphNode_t> nodes(n_all);
+            if (cudaGraphGetNodes(graph, nodes.data(), &n_all) == cudaSuccess)
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++n_nodes;
+                }
+        }
+        count_launch(-(long long)n_nodes);
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess)
+            return fail_status(LGK_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        return LGK_OK;
+    };
+    if ((rc = capture())) return rc;
     Control* hc = nullptr;
     LGK_CUDA_TRY(cudaMallocHost(&hc, sizeof(Control) * G));
     struct HostGuard {
@@ -1575,13 +1584,29 @@ int run_group(int G, ResultData* const* R) {
             std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
         bool any = false;
+        int age = 0;             // iterations of the oldest running member
         for (int g = 0; g < G; ++g) {
             if (hc[g].err)
                 return fail_status(LGK_ECUDA, "device error flag " + std::to_string(hc[g].err) +
                                                   " raised during the group solve (case " + std::to_string(g) + ")");
             any = any || hc[g].n_active != 0;
+            if (hc[g].n_active) age = std::max(age, hc[g].iter);
         }
         if (!any) break;
+        if (R[0]->refine && c0.prm.lo_refresh_iters > 0 && age >= c0.prm.lo_refresh_iters) {
+            // a member still running this long: as a solo solve does, the
+            // group continues with the literal iteration (every term every
+            // step; 128-row tiles) from the current state
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            for (int g = 0; g < G; ++g) {
+                R[g]->refine = false;
+                R[g]->force_wide = R[g]->force_wide2 = -1;
+                if ((rc = tc_prepare(*R[g]))) return rc;
+                cx[g] = make_ctx(*R[g]);
+            }
+            if ((rc = capture())) return rc;
+        }
     }
     for (int g = 0; g < G; ++g) {
         ResultData& r = *R[g];

@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     // tail.  Their bytes are added to the stage's full barrier as a pending
     // transaction without an arrival: the stage cannot complete before the
     // arrival that comes with its B tile, after the wait.  (Not for launches
-    // that work only in the solve's first iteration: they mostly do nothing.)
-    // In a group, for case 0.
+    // that work only in the solve's first iteration: they mostly do nothing;
+    // not for groups.)
     const uint32_t a_bytes = (uint32_t)(NA * MT * kABytes);
     int pre = 0;
-    if (!a0.first_only && warp == 0 && lane == 0 && (int)blockIdx.x < a0.ncta) {
+    if (G == 1 && !a0.first_only && warp == 0 && lane == 0 && (int)blockIdx.x < a0.ncta) {
         const int s0 = a0.cta_seg[blockIdx.x], s1 = a0.cta_seg[blockIdx.x + 1];
         prefetch_tmap(&P.tmA[0]);
         prefetch_tmap(&P.tmB[0]);
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_gemm(const __grid_constant__
     }
     __syncthreads();
     const int runmask = *sh_run;
-    // stages prefetched for case 0 when case 0 has stopped (or an error is
+    // stages prefetched for a solve that has stopped (or has an error
     // pending): the producer lets them land and both pipelines start after them
     const int skip = (runmask & 1) ? 0 : *sh_pre;
 

@@ -5,6 +5,10 @@ times, against stored oracle plans:
     slider weightings streamed through 32 columns, lowest BOT weight first;
   * the 5000 x 61600 four-target case (200 isocenters, 60000 points): its 441
     weightings streamed through 128 columns;
+  * the 8325 x 122664 nine-target case (333 isocenters, 120000 points): its
+    441 weightings streamed through 128 columns (stored oracle plans for four
+    weightings of the upper half of the BOT slider: the FP64 oracle on the host
+    needs hours per weighting at the lowest BOT weights);
 
 BF16X3 form with the lagged low term and one refinement step of the
 x-update's solve per iteration (lgk_params.solve_refine = 1), solved to
@@ -67,8 +71,9 @@ def load(cfg):
         return json.load(f)
 
 
-@pytest.mark.parametrize("cfg, width", [(1, 32), (2, 128)], ids=["3750x41200_k81", "5000x61600_k441"])
-def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width):
+@pytest.mark.parametrize("cfg, width, max_iter", [(1, 32, 20000), (2, 128, 20000), (3, 128, 40000)],
+                         ids=["3750x41200_k81", "5000x61600_k441", "8325x122664_k441"])
+def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width, max_iter):
     gold = load(cfg)
     case = SC.workload_case(cfg)
     grid = SC.WORKLOADS[cfg]["grid"]
@@ -79,7 +84,7 @@ def test_streamed_full_size_against_stored_oracle_plans(lgk, cfg, width):
                          case.q_area, case.q_vol, case.d_ld1, case.d_ld2, case.phi_cal,
                          params=lgk.default_params(solve_refine=1))
     assert (cs.m, cs.n) == (gold["m"], gold["n"])
-    s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=gold["rho0"], tol=SOLVE_TOL, max_iter=20000,
+    s = lgk.solve_stream(cs, W, w0_bot=SC.W0_BOT, rho0=gold["rho0"], tol=SOLVE_TOL, max_iter=max_iter,
                          width=width, check=True)
     cs.close()
     assert s["converged"].all()

@@ -83,6 +83,30 @@ def test_group_members_equal_their_solo_solves_bitwise(lgk, refine):
         c.close()
 
 
+def test_members_stop_on_their_own(lgk):
+    """The first member stops long before the second (three fast weightings
+    of the sphere case against 40 of another case): the later launches skip
+    it, and both members still equal their solo solves bit for bit."""
+    cases, Ws = members(lgk)
+    cases[1].close()
+    cases = [cases[0], cases[2]]
+    Ws = [Ws[0][[2, 5, 8]], Ws[2]]                    # the sphere's fastest weightings first
+    kw = dict(w0_bot=W0, tol=1e-4, max_iter=3000)
+    group = lgk.solve_group(cases, Ws, None, rho0=[rule(c) for c in cases], **kw)
+    solo = [lgk.solve_weightings(c, W, None, rho0=rule(c), **kw) for c, W in zip(cases, Ws)]
+    its = [int(lgk.fetch_stats(r)["iters"].max()) for r in group]
+    assert its[0] + 100 <= its[1], its
+    for a, b in zip(solo, group):
+        sa, sb = lgk.fetch_stats(a), lgk.fetch_stats(b)
+        np.testing.assert_array_equal(sb["iters"], sa["iters"])
+        np.testing.assert_array_equal(sb["obj"], sa["obj"])
+        np.testing.assert_array_equal(lgk.fetch_state(b)[0], lgk.fetch_state(a)[0])
+    for r in solo + group:
+        r.close()
+    for c in cases:
+        c.close()
+
+
 def test_a_wide_member_moves_the_group_to_128_row_tiles(lgk):
     cases, Ws = members(lgk)
     big = SC.slider_weights(13)[:150]                 # 150 weightings: no 256-row tiles
