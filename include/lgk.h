@@ -173,6 +173,14 @@ typedef struct {
                                 count allow it), or 0 (default) for GEMM1's height.  Changes the
                                 summation order (results differ in rounding).  The autotuner
                                 chooses it on its own.                                        */
+    int accum_kblocks;       /* BF16 forms: GEMM1 (A . R1, a sum over all n columns of A) keeps at
+                                most this many 64-column blocks in one tensor-memory
+                                accumulator; longer k ranges are cut into more stream-K partial
+                                sums, added in k order (round to nearest) by the next kernel.
+                                The tensor cores' FP32 accumulation over a long chain drifts
+                                (on the 8325 x 122664 case, chains of ~430 blocks left the
+                                plans' FP64 duality gap at 1-3e-3; 64 brings it to ~1e-4).
+                                Default 64; 0: no limit.                                     */
 } lgk_params;
 
 /* Fills *p with the defaults above.  Returns LGK_EINVAL if p is NULL. */

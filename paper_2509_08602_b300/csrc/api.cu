@@ -85,6 +85,7 @@ int lgk_default_params(lgk_params* p) {
     p->refine_after = 4000;
     p->l2_keep_inverse = 0;
     p->gemm2_tile_rows = 0;
+    p->accum_kblocks = 64;
     return LGK_OK;
 }
 
@@ -107,6 +108,7 @@ int lgk_create_case(const lgk_case_desc* d, const lgk_params* p, lgk_case** out)
         return fail(LGK_EINVAL, "l2_keep_inverse must be 0 or 1");
     if (prm.gemm2_tile_rows != 0 && prm.gemm2_tile_rows != 128 && prm.gemm2_tile_rows != 256)
         return fail(LGK_EINVAL, "gemm2_tile_rows must be 0, 128 or 256");
+    if (prm.accum_kblocks < 0) return fail(LGK_EINVAL, "accum_kblocks must be >= 0");
     if (prm.precision != LGK_PREC_FP32 && prm.precision != LGK_PREC_BF16 &&
         prm.precision != LGK_PREC_BF16X3)
         return fail(LGK_EINVAL, "unknown precision");

@@ -850,7 +850,9 @@ int tc_prepare(ResultData& r) {
                                  : (p2 == 128 ? false : p2 == 256 ? can_wide : r.wide);
     const int hm = r.wide ? 2 : 1, hm2 = r.wide2 ? 2 : 1;
     const int mt = cs.m_pad / 128, nt = cs.n_pad / 128;
-    if ((rc = build_plan(r.plan1, mt / hm, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false, hm))) return rc;
+    if ((rc = build_plan(r.plan1, mt / hm, r.Kp / r.n_tile, cs.n_pad / 64, r.n_tile, false, hm,
+                         cs.prm.accum_kblocks)))
+        return rc;
     if ((rc = build_plan(r.plan_s, mt, r.Kp / r.n_tile_s, cs.m_pad / 64, r.n_tile_s, false, 1))) return rc;
     if ((rc = build_plan(r.plan2, nt / hm2, r.Kp / r.n_tile, cs.m_pad / 64, r.n_tile, true, hm2))) return rc;
     size_t slots = std::max({(size_t)r.plan1.nseg * r.n_tile * hm, (size_t)r.plan_s.nseg * r.n_tile_s,

@@ -46,7 +46,8 @@ class Params(C.Structure):
                 ("profile", C.c_int), ("lo_refresh", C.c_int), ("lo_refresh_iters", C.c_int),
                 ("rho_adapt", C.c_int), ("solve_refine", C.c_int), ("setup_fp64", C.c_int),
                 ("check_fp64", C.c_int), ("autotune", C.c_int), ("refine_after", C.c_int),
-                ("l2_keep_inverse", C.c_int), ("gemm2_tile_rows", C.c_int)]
+                ("l2_keep_inverse", C.c_int), ("gemm2_tile_rows", C.c_int),
+                ("accum_kblocks", C.c_int)]
 
 
 class ServerParams(C.Structure):

@@ -113,7 +113,10 @@ def test_a_wide_member_moves_the_group_to_128_row_tiles(lgk):
     Ws = [Ws[0], big]
     cases[2].close()
     cases = cases[:2]
-    kw = dict(w0_bot=W0, tol=1e-4, max_iter=6000)
+    # both sides stop at 5e-5, as the converged parity tests do: two plans
+    # stopped at 1e-4 on differently rounded paths can sit just over 1e-3
+    # apart in objective on these degenerate LPs
+    kw = dict(w0_bot=W0, tol=5e-5, max_iter=8000)
     group = lgk.solve_group(cases, Ws, None, rho0=[rule(c) for c in cases], **kw)
     solo = [lgk.solve_weightings(c, W, None, rho0=rule(c), **kw) for c, W in zip(cases, Ws)]
     for a, b in zip(solo, group):
