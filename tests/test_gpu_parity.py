@@ -35,7 +35,7 @@ TOL = 1e-4
 # Converged solves stop at 5e-5: a stop at relative residual 1e-4 leaves the
 # objective within about 1e-3 of the optimum, not below it (one weighting of
 # the BF16X3 form stops at 1.01e-3 to 1.05e-3, depending on the rounding
-# order of S), so solving to 5e-5 meets both the benchmark spec gates (residuals
+# order of S), so solving to 5e-5 meets both parity gates (residuals
 # <= 1e-4, objective gap <= 1e-3) with headroom.  The oracle reference plans
 # stop at the same tolerance: these LPs are degenerate in the sector times
 # (plans are compared with the oracle's ADMM plan from the same start and
