@@ -128,3 +128,19 @@ def test_null_arguments_are_errors_not_crashes(lgk):
     lib.lgk_free_result(None)
     lib.lgk_destroy_case(None)
     assert b"NULL" in lib.lgk_last_error() or len(lib.lgk_last_error()) > 0
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: include/lgk.h compiles as C99 on its own
+    (no C++ or CUDA types in the declarations)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_lgk.c"
+    src.write_text('#include "lgk.h"\n'
+                   "int main(void) { lgk_params p; return lgk_default_params(&p); }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
