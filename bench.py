@@ -1,7 +1,7 @@
 #!/usr/bin/env python3
 """Converged plans/s of batched ADMM planning on one B300 (and N replicas).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg1|cfg2|cfg0]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg0|cfg1|cfg2|cfg3]
     python bench.py --impl reference ...     # the FP64 CPU oracle on host cores
 
 A step is one solve of the whole hot path over one batch of weightings: K
@@ -516,18 +516,30 @@ def run_ours(args, rank, world, local):
             cpu = oracle_sample(case, W, n_iters, basis)
         if not args.no_extras and r_last is None:     # streaming: one batch solve for the extras
             r_last = lgk.solve_weightings(cs, W, None, **rule)
-        extra = {} if args.no_extras else {
-            "plan_metrics": bench_metrics(lgk, case, r_last),
-            "two_pass": bench_two_pass(lgk, case, W, args, local)}
+        # the measurements beside the main line: a failure in one is recorded
+        # in its key and does not take the main line down with it
+        extra = {}
+
+        def leg(name, fn):
+            try:
+                extra[name] = fn()
+            except Exception as e:          # noqa: BLE001 (reported in the line)
+                extra[name] = {"error": f"{type(e).__name__}: {e}"[:400]}
+
+        if not args.no_extras:
+            leg("plan_metrics", lambda: bench_metrics(lgk, case, r_last))
+            leg("two_pass", lambda: bench_two_pass(lgk, case, W, args, local))
         if not args.no_k441 and args.workload == "cfg1":
-            extra["k441"] = bench_k441(lgk, args, local)
+            leg("k441", lambda: bench_k441(lgk, args, local))
         if not args.no_group and args.workload == "cfg1":
-            extra["group"] = bench_group(lgk, args, local, with_cfg3=args.group_cfg3)
+            leg("group", lambda: bench_group(lgk, args, local, with_cfg3=args.group_cfg3))
         if not args.no_serve and args.workload == "cfg1":
-            sv = serve_run(lgk, args, local, n_cases=24, rate=1.0, workers=2)
-            sv["note"] = ("a short stream of the serving workload (bench.py --serve N sweeps the "
-                          "arrival rate); latency = submit to results")
-            extra["serving"] = sv
+            def serving():
+                sv = serve_run(lgk, args, local, n_cases=24, rate=1.0, workers=2)
+                sv["note"] = ("a short stream of the serving workload (bench.py --serve N sweeps the "
+                              "arrival rate); latency = submit to results")
+                return sv
+            leg("serving", serving)
         lat_ms = sorted(x * 1e3 for x in lat)
         out = {"metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
